@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the VP-LBM hot path on GB300.
+
+Workload: NACA 0012 at Re 1000 on a 2048 x 1024 FP32 lattice (chord 200),
+the five angles 0, 5, 10, 15, 20 degrees as five resident lattices.  One
+benchmark step advances every lattice by one time step: the fused
+collide-penalize-stream kernel with the MEM force and the SIM force (849
+points) of that step.  Metric: million lattice-node updates per second
+(MLUPS) over all lattices and ranks.  The five lattices hold 5 x 151 MB of
+populations, more than the 129 MB L2, and are stepped in turn.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs the five lattices on its own GPU (weak
+scaling; no collective on the data path).  --impl reference times the FP64
+CPU oracle on the host cores on the same workload (one lattice-step per
+benchmark step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ANGLES = (0.0, 5.0, 10.0, 15.0, 20.0)
+NX, NY = 2048, 1024
+BYTES_PER_LUP = 9 * 4 + 9 * 4 + 1  # FP32 populations read + written, mask byte
+PROFILE = os.path.join(ROOT, "profiles", "step_kernel_naca2048_f32.md")
+KERNEL_SOURCES = ("paper_2110_00967_gb300/csrc/step.cu",
+                  "paper_2110_00967_gb300/csrc/vplbm_internal.cuh")
+METRIC = "VP-LBM MLUPS"
+WORKLOAD = "naca0012-re1000-2048x1024-f32-alpha0,5,10,15,20"
+
+
+def config_block(extra=None):
+    c = {"workload": WORKLOAD, "grid": [NX, NY], "instances": len(ANGLES), "chord": 200,
+         "reynolds": 1000, "tau_plus": 0.53, "collision": "trt-lambda-1/6",
+         "forces_per_step": ["mem", "sim-849"],
+         "l2": "inputs larger than L2: 5 lattices x 151 MB ping-pong, stepped in turn"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def kernel_sources_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != kernel_sources_hash():
+        return None
+    return float(m.group(1))
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# multi-rank plumbing (also exercised with gloo on CPU by the tests)
+# ---------------------------------------------------------------------------
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_instance(alpha: float):
+    import oracle as o
+    from paper_2110_00967_gb300 import workloads as W
+    w = W.naca(alpha, dtype="f64")
+    cfg = o.make_config(w.nx, w.ny, bc=(o.BC_INLET, o.BC_OUTLET, o.BC_SYMMETRY, o.BC_SYMMETRY),
+                        collision=o.TRT, tau_plus=w.tau_plus, lambda_trt=w.lambda_trt,
+                        eta=w.eta, u_in=w.u_in)
+    body = o.make_body(o.BODY_NACA, length=w.body.length, thickness=w.body.thickness,
+                       xg=w.body.x_c, yg=w.body.y_c, theta=w.body.angle,
+                       pivot_frac=w.body.pivot_chord_frac)
+    chi = o.raster(body, w.nx, w.ny)
+    f = o.init(cfg, body, chi)
+    return cfg, body, chi, f, o.sim_points(body)
+
+
+def time_oracle(steps: int, warmup: int):
+    """Oracle steps (collision, MEM, SIM, streaming) of the 10-degree lattice."""
+    import oracle as o
+    cores = o.set_threads(os.cpu_count() or 1)
+    cfg, body, chi, f, pts = oracle_instance(10.0)
+    if warmup:
+        o.run(cfg, body, f, chi, warmup, sim_pts=pts, histories=False)
+    t0 = time.perf_counter()
+    o.run(cfg, body, f, chi, steps, sim_pts=pts, histories=False)
+    dt = time.perf_counter() - t0
+    return NX * NY * steps / dt / 1e6, dt, cores
+
+
+def cpu_baseline_block(budget_s: float = 12.0):
+    import oracle as o
+    cores = o.set_threads(os.cpu_count() or 1)
+    cfg, body, chi, f, pts = oracle_instance(10.0)
+    t0 = time.perf_counter()
+    o.run(cfg, body, f, chi, 1, sim_pts=pts, histories=False)
+    one = time.perf_counter() - t0
+    n = int(max(1, min(200, budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    o.run(cfg, body, f, chi, n, sim_pts=pts, histories=False)
+    dt = time.perf_counter() - t0
+    return {"value": round(NX * NY * n / dt / 1e6, 3), "unit": "MLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{n} steps of the 10-degree 2048x1024 lattice (FP64 C oracle, "
+                      f"{cores} OpenMP threads), {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2110_00967_gb300 import vplbm as V
+    from paper_2110_00967_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    works = [W.naca(a, dtype="f32") for a in ANGLES]
+    lats = [V.Lattice(V.config_of(w), device=dev) for w in works]
+    for w, lat in zip(works, lats):
+        lat.set_body(V.body_of(w))
+
+    def one_step():
+        for lat in lats:
+            lat.step(1)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # device-timed region
+    n_ev = min(2000, args.steps * len(lats))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(n_ev)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = sum(l.launches for l in lats)
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    k = 0
+    start.record(stream)
+    for _ in range(args.steps):
+        for lat in lats:
+            if k < n_ev:
+                evs[k][0].record(stream)
+                lat.step(1)
+                evs[k][1].record(stream)
+            else:
+                lat.step(1)
+            k += 1
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    barrier(world)
+    launches = sum(l.launches for l in lats) - l0
+    elapsed_ms = reduce_max(start.elapsed_time(end), world, dev)
+    # per-launch device time; the first launches of the region are skipped
+    # while the launch queue fills
+    kern_ms = [a.elapsed_time(b) for a, b in evs][min(10, n_ev // 2):]
+    kern_avg_ms = sum(kern_ms) / len(kern_ms)
+    for lat in lats:
+        lat.check()
+
+    # end-to-end through the public API: place the bodies (host geometry up),
+    # step, and read every step's forces back into pinned host memory
+    e2e_steps = max(50, min(args.steps, 2000))
+    pinned = torch.empty((e2e_steps, len(lats), 6), dtype=torch.float64, pin_memory=True)
+    lats2 = lats  # reuse the workspaces; set_body restarts each solve
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for w, lat in zip(works, lats2):
+        lat.set_body(V.body_of(w))
+    for s in range(e2e_steps):
+        for i, lat in enumerate(lats2):
+            lat.step(1)
+            V.vplbm_forces_async(lat.ctx, pinned[s, i].data_ptr())
+    torch.cuda.synchronize()
+    e2e_dt = reduce_max(time.perf_counter() - t0, world, dev)
+    assert bool(torch.isfinite(pinned[-1]).all())
+    body_bytes = 16 * 8 + 4 * 4  # device body state block
+    sim_bytes = 849 * 48
+    h2d = len(lats) * (body_bytes + sim_bytes) / e2e_steps
+    d2h = len(lats) * 6 * 8
+
+    nodes = NX * NY * len(lats)
+    value = world * nodes * args.steps / (elapsed_ms / 1e3) / 1e6
+    e2e_value = world * nodes * e2e_steps / e2e_dt / 1e6
+    peak, peak_kind = measured_hbm_peak()
+    achieved = BYTES_PER_LUP * NX * NY / (kern_avg_ms / 1e3) / 1e9
+    traffic = profiled_traffic()
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_block({"parallelism": f"replicas{world}"}),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "step_kernel<float,true>",
+                     "kernel_avg_us": round(kern_avg_ms * 1e3, 3),
+                     "bytes_per_lup": BYTES_PER_LUP, "peak_kind": peak_kind},
+        "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS",
+                "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_block()
+    return line
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    mlups, dt, cores = time_oracle(args.steps, args.warmup)
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_block({"reference_sample": "one step of the 10-degree lattice per "
+                                                    "benchmark step"}),
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{args.steps} steps of the 10-degree 2048x1024 lattice"},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        from __graft_entry__ import build
+        build()
+        line = run_ours(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

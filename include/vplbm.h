@@ -1,0 +1,230 @@
+/*
+ * vplbm.h -- C ABI of a GB300 (sm_103a) volume-penalized lattice Boltzmann
+ * solver: D2Q9 VP-LBM with the two fluid-force estimators compared by
+ * Liberge & Beghein, "About fluid forces computation for Volume Penalization
+ * coupled with Lattice Boltzmann method" (arXiv 2110.00967).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a vplbm_status and never aborts, exits or prints.
+ *     The text of the last failure is available from vplbm_last_error().
+ *   - The library never allocates device memory.  The caller hands it one
+ *     device workspace at creation (vplbm_workspace_bytes tells the size) and
+ *     owns it; vplbm_destroy does not free it.  Pointers documented as
+ *     "device" are caller-owned device memory, pointers documented as "host"
+ *     are caller-owned host memory.
+ *   - All GPU work is queued on the caller's CUDA stream given at creation
+ *     (or vplbm_set_stream).  vplbm_step only queues work; calls that return
+ *     host values synchronise that stream.
+ *   - Lattice node (i, j) sits at x = i, y = j (lattice units, dx = dt = 1);
+ *     i runs fastest.  Fields of a lattice are laid out [j][i]; populations
+ *     are laid out [a][j][i] with the D2Q9 numbering of the paper's Fig. d2q9:
+ *     a = 0 rest, 1 (1,0), 2 (0,1), 3 (-1,0), 4 (0,-1), 5 (1,1), 6 (-1,1),
+ *     7 (-1,-1), 8 (1,-1).
+ *   - Forces are the force exerted by the fluid on the body (Eqs. MMEL and
+ *     defFf); torques are taken about the body reference point (x_c, y_c).
+ */
+#ifndef VPLBM_H
+#define VPLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vplbm_ctx vplbm_ctx;
+
+typedef enum {
+  VPLBM_OK = 0,
+  VPLBM_EINVAL = 1,    /* bad argument or configuration */
+  VPLBM_ENOMEM = 2,    /* workspace too small */
+  VPLBM_ECUDA = 3,     /* a CUDA runtime call failed */
+  VPLBM_EUNSTABLE = 4, /* a non-finite or non-positive density was met (latched) */
+  VPLBM_ETIMEOUT = 5,  /* a bounded device-side wait ran out */
+  VPLBM_ESTATE = 6     /* call not valid in the current state (no body, no step yet,
+                          SIM point without a fluid node) */
+} vplbm_status;
+
+/* Storage of the populations.  All forms store the offsets h_a = f_a - w_a
+ * (w_a the lattice weights).  F64 computes in FP64; F32, F16_OFS and BF16_OFS
+ * compute the step in FP32 (the 16-bit forms round to nearest even on store).
+ * Force reductions and the rigid-body update are FP64 in every form. */
+typedef enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFS = 2, VPLBM_BF16_OFS = 3 } vplbm_dtype;
+
+/* Collision operator: BGK (Sec. 2.2) or TRT (Eq. TRT) with
+ * tau- = Lambda / (tau+ - 1/2) + 1/2. */
+typedef enum { VPLBM_BGK = 0, VPLBM_TRT = 1 } vplbm_collision;
+
+/* How the forcing term F_a (Guo et al., cited with Eq. eqBd) enters TRT:
+ * PAPER multiplies all of F_a by (1 - 1/(2 tau+)) as Eq. TRT prints it;
+ * SPLIT multiplies its antisymmetric part by (1 - 1/(2 tau-)) instead.
+ * Both are the same for BGK. */
+typedef enum { VPLBM_FORCING_PAPER = 0, VPLBM_FORCING_SPLIT = 1 } vplbm_forcing;
+
+/* Side conditions (Sec. 3.1 and 3.2).  x sides: PERIODIC (both), INLET_BB
+ * (half-way bounce-back from a wall moving at u_in), OUTLET_CONVECTIVE (x_hi
+ * only; convective condition with U_c = |u_in|), NOSLIP_BB.  y sides:
+ * PERIODIC (both), SYMMETRY (specular reflection), NOSLIP_BB.  Walls sit half
+ * a cell beyond the edge nodes. */
+typedef enum {
+  VPLBM_PERIODIC = 0,
+  VPLBM_INLET_BB = 1,
+  VPLBM_OUTLET_CONVECTIVE = 2,
+  VPLBM_SYMMETRY = 3,
+  VPLBM_NOSLIP_BB = 4
+} vplbm_bc;
+
+typedef enum { VPLBM_BODY_NONE = 0, VPLBM_BODY_DISK = 1, VPLBM_BODY_NACA4 = 2 } vplbm_body_kind;
+
+typedef enum { VPLBM_MEM = 0, VPLBM_SIM = 1 } vplbm_estimator;
+
+typedef struct {
+  int32_t nx, ny;          /* lattice size, each >= 3 */
+  int32_t dtype;           /* vplbm_dtype */
+  int32_t collision;       /* vplbm_collision */
+  int32_t forcing;         /* vplbm_forcing */
+  int32_t bc[4];           /* vplbm_bc for x_lo, x_hi, y_lo, y_hi */
+  int32_t sim_every;       /* evaluate SIM every k-th step (0: never) */
+  int32_t max_sim_points;  /* capacity for SIM points (0: 4096) */
+  int32_t history_len;     /* per-step force history ring length (0: 1024) */
+  double tau_plus;         /* > 1/2; nu = (tau+ - 1/2)/3 (Eq. tauvisco) */
+  double lambda_trt;       /* TRT magic parameter Lambda (1/6 in Sec. 2.2) */
+  double eta;              /* penalization factor, > 0 (1e-6 in Sec. 3) */
+  double u_in[2];          /* inlet velocity and the initial fluid velocity */
+  double body_force[2];    /* uniform force density on every node (0 in the paper) */
+} vplbm_config;
+
+typedef struct {
+  int32_t kind;            /* vplbm_body_kind */
+  int32_t moving;          /* 1: integrate Eqs. dep1 and theta2 each step (disk only) */
+  int32_t n_sim_points;    /* SIM points (0: disk ceil(2 pi R / 0.5), airfoil 849);
+                              airfoil counts are odd */
+  int32_t estimator;       /* vplbm_estimator driving a moving body */
+  double length;           /* disk diameter D or chord C (lattice units) */
+  double thickness;        /* NACA 4-digit thickness ratio t (0.12); ignored for a disk */
+  double x_c, y_c;         /* disk centre, or airfoil pivot point */
+  double angle;            /* airfoil angle of attack in radians, positive nose up;
+                              disk: initial rotation angle */
+  double pivot_chord_frac; /* airfoil pivot position along the chord (0.25) */
+  double u[2];             /* rigid translational velocity */
+  double omega;            /* rigid angular velocity (counter-clockwise) */
+  double density_ratio;    /* rho_s / rho (moving body) */
+  double gravity[2];       /* gravity acting on a moving body (Eq. dep1) */
+} vplbm_body;
+
+/* Device bytes a lattice with this configuration needs (population ping-pong
+ * buffers, mask, outlet column, force partials, SIM points, histories).
+ * Returns EINVAL for an invalid configuration (same checks as vplbm_create). */
+vplbm_status vplbm_workspace_bytes(const vplbm_config *cfg, size_t *bytes);
+
+/* Creates a lattice in the caller's device workspace (dev_workspace, at least
+ * vplbm_workspace_bytes, 256-byte aligned) on the device that is current.
+ * cuda_stream is a cudaStream_t (NULL: the legacy default stream).  EINVAL on
+ * nx or ny < 3, tau+ <= 1/2, eta <= 0, a bad side combination or dtype;
+ * ENOMEM when bytes is too small.  The lattice holds no body until
+ * vplbm_set_body. */
+vplbm_status vplbm_create(const vplbm_config *cfg, void *dev_workspace, size_t bytes,
+                          void *cuda_stream, vplbm_ctx **out);
+
+/* Replaces the stream used by later calls. */
+vplbm_status vplbm_set_stream(vplbm_ctx *ctx, void *cuda_stream);
+
+/* Places the body: rasterises chi (Eq. fcar: 1 on nodes inside or on the
+ * body), builds the SIM polygon (Eq. defFf quadrature, points on the body
+ * surface with their outward normals and lengths), resets the step counter,
+ * force histories and averages, and sets the initial state f = feq(1, u0)
+ * with u0 = u_in on fluid nodes and the rigid velocity on solid nodes.
+ * kind NONE gives an empty lattice.  EINVAL when the body does not fit in
+ * the lattice, n_sim_points exceeds the capacity, or a NACA body is moving. */
+vplbm_status vplbm_set_body(vplbm_ctx *ctx, const vplbm_body *body);
+
+/* Queues nsteps time steps (nsteps >= 0).  One step, for every node:
+ * moments and penalized velocity (Eqs. updatestep .. updatestepm), force
+ * density G = -rho (chi/eta)(u - u_s) + body force, equilibrium and
+ * collision with the forcing term (Eq. TRT / BGK), streaming with the side
+ * conditions (Eq. eqBd, Sec. 3.1); the MEM force of Eq. MMEL / Eq. fluidtorque
+ * on the post-collision populations; the SIM force of Eq. defFf on the
+ * pre-collision populations (when due); and, for a moving body, the FP64
+ * rigid-body update of Eqs. dep1 / theta2 followed by re-rasterising chi. */
+vplbm_status vplbm_step(vplbm_ctx *ctx, int32_t nsteps);
+
+/* Force (F[0], F[1]) and torque (*T) of the last step from MEM (Eq. MMEL,
+ * Eq. fluidtorque), host outputs.  Synchronises the stream.  ESTATE before the
+ * first step; EUNSTABLE when the instability flag is set. */
+vplbm_status vplbm_force_mem(vplbm_ctx *ctx, double F[2], double *T);
+
+/* Same for SIM (Eq. defFf): the last step on which SIM was evaluated.
+ * ESTATE when SIM has not run or a point found no fluid node. */
+vplbm_status vplbm_force_sim(vplbm_ctx *ctx, double F[2], double *T);
+
+/* Queues a copy of the last step's forces into caller host memory without
+ * waiting: out[6] = MEM (F_x, F_y, T) then SIM (F_x, F_y, T) (SIM entries are
+ * NaN on steps where SIM was not evaluated).  out should be page-locked for
+ * the copy to be asynchronous; it is valid once the stream has been
+ * synchronised.  ESTATE before the first step. */
+vplbm_status vplbm_forces_async(vplbm_ctx *ctx, double *out);
+
+/* Last `count` per-step forces of one estimator, oldest first, host output
+ * out[count][3] = (F_x, F_y, T).  EINVAL when count exceeds the history length
+ * or the number of steps taken. */
+vplbm_status vplbm_force_history(vplbm_ctx *ctx, int32_t estimator, int32_t count, double *out);
+
+/* FP64 sums of (F_x, F_y, T) of both estimators since the last reset and the
+ * number of steps summed (host outputs sums[6] = MEM then SIM, n[2]). */
+vplbm_status vplbm_force_sums(vplbm_ctx *ctx, double sums[6], int64_t n[2]);
+vplbm_status vplbm_reset_sums(vplbm_ctx *ctx);
+
+/* Number of steps taken since vplbm_set_body (host output). */
+vplbm_status vplbm_step_count(vplbm_ctx *ctx, int64_t *n);
+
+/* Pre-collision populations f_a of the current time level as FP64 into the
+ * caller's device buffer f_dev[9][ny][nx] (the streamed field: Eq. eqBd's
+ * left-hand side).  Queued on the stream. */
+vplbm_status vplbm_get_f(vplbm_ctx *ctx, double *f_dev);
+
+/* Macroscopic fields of the current time level (Eqs. updatestep,
+ * updatestepm) as FP64 into caller device buffers [ny][nx] each.  Queued. */
+vplbm_status vplbm_get_fields(vplbm_ctx *ctx, double *rho_dev, double *ux_dev, double *uy_dev);
+
+/* Overwrites the state from caller device FP64 buffers [9][ny][nx].
+ * post_collision = 0: f_dev is the pre-collision field of the current time
+ * level (prev_dev ignored).  post_collision = 1: f_dev is the post-collision
+ * field of the previous level and prev_dev that level's pre-collision field
+ * (only its x_hi column is read, for the convective outlet; may be NULL when
+ * x_hi is not an outlet).  Converted to the storage form (16-bit forms round
+ * to nearest even).  The step counter is kept.  Queued. */
+vplbm_status vplbm_set_state(vplbm_ctx *ctx, const double *f_dev, const double *prev_dev,
+                             int32_t post_collision);
+
+/* Mask chi of the current time level (0 fluid, 1 solid) into caller device
+ * memory [ny][nx] bytes.  Queued. */
+vplbm_status vplbm_get_mask(vplbm_ctx *ctx, uint8_t *chi_dev);
+
+/* Body state (x_c, y_c, angle, u_x, u_y, omega), host output.  Synchronises. */
+vplbm_status vplbm_get_body(vplbm_ctx *ctx, double state[6]);
+
+/* Lattice node index j*nx + i sampled by each SIM point at its last
+ * evaluation (-1: none), host output nodes[n_sim_points]; *n gets the count.
+ * Synchronises. */
+vplbm_status vplbm_get_sim_nodes(vplbm_ctx *ctx, int32_t *nodes, int32_t capacity, int32_t *n);
+
+/* Latched device status: OK, EUNSTABLE or ETIMEOUT.  Synchronises. */
+vplbm_status vplbm_check(vplbm_ctx *ctx);
+
+/* Number of kernels the library has launched on this lattice so far. */
+vplbm_status vplbm_launch_count(vplbm_ctx *ctx, int64_t *n);
+
+/* Releases the host-side context; never touches the caller's workspace.
+ * NULL is accepted. */
+void vplbm_destroy(vplbm_ctx *ctx);
+
+/* Text of the last failure on ctx (never NULL; "" when none).  ctx may be
+ * NULL for failures of vplbm_create / vplbm_workspace_bytes. */
+const char *vplbm_last_error(const vplbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VPLBM_H */

@@ -1,0 +1,713 @@
+// api.cu -- the C ABI of include/vplbm.h: validation, workspace carving,
+// body placement (SIM polygon of Eq. defFf built on the host in FP64), step
+// scheduling with CUDA-graph replay, and read-back of forces and fields.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vplbm_internal.cuh"
+
+using namespace vplbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kGraphPairs = 16;  // a captured graph holds 2 * kGraphPairs steps
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t elem_bytes(int dtype) {
+  switch (dtype) {
+    case VPLBM_F64: return 8;
+    case VPLBM_F32: return 4;
+    case VPLBM_F16_OFS:
+    case VPLBM_BF16_OFS: return 2;
+  }
+  return 0;
+}
+
+struct Layout {
+  size_t buf[2], prev[2], chi, partials, sim_pts, sim_contrib, sim_nodes, hist, body, sums,
+      counts, dev_step, ticket, status, total;
+};
+
+int effective_max_sim(const vplbm_config &c) { return c.max_sim_points > 0 ? c.max_sim_points : 4096; }
+int effective_hist(const vplbm_config &c) { return c.history_len > 0 ? c.history_len : 1024; }
+int pitch_of(int nx) { return (int)align_up((size_t)nx, 64); }
+
+Layout make_layout(const vplbm_config &c) {
+  Layout l{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, kAlign);
+    return at;
+  };
+  const size_t plane = (size_t)pitch_of(c.nx) * (size_t)c.ny;
+  const size_t fbytes = 9 * plane * elem_bytes(c.dtype);
+  l.buf[0] = take(fbytes);
+  l.buf[1] = take(fbytes);
+  l.prev[0] = take(3 * (size_t)c.ny * sizeof(double));
+  l.prev[1] = take(3 * (size_t)c.ny * sizeof(double));
+  l.chi = take(plane);
+  l.partials = take((size_t)kMaxBlocks * 3 * sizeof(double));
+  const size_t ms = (size_t)effective_max_sim(c);
+  l.sim_pts = take(ms * sizeof(SimPoint));
+  l.sim_contrib = take(ms * 3 * sizeof(double));
+  l.sim_nodes = take(ms * sizeof(int32_t));
+  l.hist = take((size_t)effective_hist(c) * 6 * sizeof(double));
+  l.body = take(sizeof(BodyState));
+  l.sums = take(6 * sizeof(double));
+  l.counts = take(2 * sizeof(long long));
+  l.dev_step = take(sizeof(long long));
+  l.ticket = take(sizeof(unsigned int));
+  l.status = take(sizeof(int32_t));
+  l.total = off;
+  return l;
+}
+
+std::string g_err;  // failures of calls without a context (create / workspace_bytes)
+
+std::string fmt(const char *f, ...) {
+  char b[512];
+  va_list ap;
+  va_start(ap, f);
+  vsnprintf(b, sizeof b, f, ap);
+  va_end(ap);
+  return b;
+}
+
+const char *check_config(const vplbm_config *c) {
+  if (!c) return "config is NULL";
+  if (c->nx < 3 || c->ny < 3) return "nx and ny must be >= 3";
+  if ((int64_t)c->nx * c->ny > (int64_t)1 << 31) return "lattice too large";
+  if (elem_bytes(c->dtype) == 0) return "unknown dtype";
+  if (c->collision != VPLBM_BGK && c->collision != VPLBM_TRT) return "unknown collision";
+  if (c->forcing != VPLBM_FORCING_PAPER && c->forcing != VPLBM_FORCING_SPLIT) return "unknown forcing";
+  if (!(c->tau_plus > 0.5) || !std::isfinite(c->tau_plus)) return "tau_plus must be > 1/2";
+  if (c->collision == VPLBM_TRT && !(c->lambda_trt > 0.0)) return "lambda_trt must be > 0";
+  if (!(c->eta > 0.0)) return "eta must be > 0";
+  if (c->sim_every < 0 || c->max_sim_points < 0 || c->history_len < 0) return "negative count";
+  for (int k = 0; k < 2; ++k)
+    if (!std::isfinite(c->u_in[k]) || !std::isfinite(c->body_force[k])) return "non-finite velocity or force";
+  const int x0 = c->bc[0], x1 = c->bc[1], y0 = c->bc[2], y1 = c->bc[3];
+  auto xok = [](int b) {
+    return b == VPLBM_PERIODIC || b == VPLBM_INLET_BB || b == VPLBM_OUTLET_CONVECTIVE || b == VPLBM_NOSLIP_BB;
+  };
+  auto yok = [](int b) { return b == VPLBM_PERIODIC || b == VPLBM_SYMMETRY || b == VPLBM_NOSLIP_BB; };
+  if (!xok(x0) || !xok(x1) || !yok(y0) || !yok(y1)) return "side condition not allowed on that side";
+  if (x0 == VPLBM_OUTLET_CONVECTIVE) return "the convective outlet is an x_hi condition";
+  if ((x0 == VPLBM_PERIODIC) != (x1 == VPLBM_PERIODIC)) return "x periodicity must hold on both sides";
+  if ((y0 == VPLBM_PERIODIC) != (y1 == VPLBM_PERIODIC)) return "y periodicity must hold on both sides";
+  return nullptr;
+}
+
+double naca_yt(double t, double xi) {
+  return 5.0 * t *
+         (0.2969 * sqrt(xi) - 0.1260 * xi - 0.3516 * (xi * xi) + 0.2843 * (xi * xi * xi) -
+          0.1015 * (xi * xi * xi * xi));
+}
+
+// Closed counter-clockwise polygon on the body surface; one SIM point per
+// edge at its midpoint with the outward normal and the edge length.
+bool build_polygon(const vplbm_body &b, int n, std::vector<SimPoint> &pts) {
+  std::vector<double> vx, vy;
+  if (b.kind == VPLBM_BODY_DISK) {
+    if (n < 3) return false;
+    const double r = 0.5 * b.length;
+    for (int k = 0; k < n; ++k) {
+      const double th = 2.0 * M_PI * (double)k / (double)n;
+      vx.push_back(r * cos(th));
+      vy.push_back(r * sin(th));
+    }
+  } else if (b.kind == VPLBM_BODY_NACA4) {
+    if (n < 5 || n % 2 == 0) return false;
+    const int m = (n - 1) / 2;
+    const double ca = cos(b.angle), sa = sin(b.angle);
+    auto put = [&](int k, double sign) {
+      const double xi = 0.5 * (1.0 - cos(M_PI * (double)k / (double)m));
+      const double zt = sign * naca_yt(b.thickness, xi);
+      const double s = (xi - b.pivot_chord_frac) * b.length, z = zt * b.length;
+      vx.push_back(s * ca + z * sa);
+      vy.push_back(-s * sa + z * ca);
+    };
+    for (int k = m; k >= 0; --k) put(k, 1.0);  // upper surface, trailing to leading edge
+    for (int k = 1; k <= m; ++k) put(k, -1.0); // lower surface, back to the trailing edge
+  } else {
+    return false;
+  }
+  const int nv = (int)vx.size();
+  if (nv != n) return false;
+  pts.resize(n);
+  for (int k = 0; k < nv; ++k) {
+    const int k2 = (k + 1) % nv;
+    const double ex = vx[k2] - vx[k], ey = vy[k2] - vy[k];
+    const double len = sqrt(ex * ex + ey * ey);
+    SimPoint &p = pts[k];
+    p.dx = 0.5 * (vx[k] + vx[k2]);
+    p.dy = 0.5 * (vy[k] + vy[k2]);
+    p.nx = ey / len;
+    p.ny = -ex / len;
+    p.s = len;
+    // lattice direction closest to the normal, ties to the lowest index
+    int best = 1;
+    double bv = -1e300;
+    for (int a = 1; a < 9; ++a) {
+      const double cl = a <= 4 ? 1.0 : sqrt(2.0);
+      const double v = (cx_of(a) * p.nx + cy_of(a) * p.ny) / cl;
+      if (v > bv) {
+        bv = v;
+        best = a;
+      }
+    }
+    p.dir = best;
+    p.pad = 0;
+  }
+  return true;
+}
+
+int default_sim_points(const vplbm_body &b) {
+  if (b.n_sim_points > 0) return b.n_sim_points;
+  if (b.kind == VPLBM_BODY_DISK) return (int)ceil(2.0 * M_PI * (0.5 * b.length) / 0.5);
+  return 849;
+}
+
+}  // namespace
+
+struct vplbm_ctx {
+  vplbm_config cfg;
+  Lattice L;
+  Layout lay;
+  cudaStream_t stream;
+  cudaStream_t capture_stream = nullptr;
+  int device;
+  char *ws;
+  void *buf[2];
+  double *prev[2];
+  uint8_t *chi;
+  double *partials;
+  SimPoint *sim_pts;
+  double *sim_contrib;
+  int32_t *sim_nodes;
+  double *hist;
+  BodyState *body;
+  double *sums;
+  long long *counts;
+  long long *dev_step;
+  unsigned int *ticket;
+  int32_t *status;
+  int cur = 0;        // buffer holding the state
+  bool pre = true;    // the state is a pre-collision field (first step reads in place)
+  bool has_body = false;
+  vplbm_body body_cfg{};
+  BodyState body_host{};
+  int n_sim = 0;
+  int sim_every = 0;  // effective
+  long long steps = 0;
+  int grid = 1;
+  int64_t launches = 0;
+  cudaGraphExec_t graph = nullptr;  // 2 * kGraphPairs steps starting from buffer 0
+  std::string err;
+  double s_plus, s_minus, a_plus, a_minus, half_pen;
+};
+
+namespace {
+
+vplbm_status fail(vplbm_ctx *c, vplbm_status st, const std::string &msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_err = msg;
+  return st;
+}
+
+vplbm_status cuda_fail(vplbm_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, VPLBM_ECUDA, fmt("%s: %s", where, cudaGetErrorString(e)));
+}
+
+#define VPLBM_CUDA(ctx, expr)                                  \
+  do {                                                         \
+    cudaError_t e_ = (expr);                                   \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #expr); \
+  } while (0)
+
+StepArgs step_args(vplbm_ctx *c, int src, bool do_sim) {
+  StepArgs a{};
+  a.L = c->L;
+  a.src = c->buf[src];
+  a.dst = c->buf[1 - src];
+  a.prev_src = c->prev[src];
+  a.prev_dst = c->prev[1 - src];
+  a.chi = c->chi;
+  a.body = c->body;
+  a.mem_partials = c->partials;
+  a.sim_pts = c->sim_pts;
+  a.sim_contrib = c->sim_contrib;
+  a.sim_nodes = c->sim_nodes;
+  a.n_sim = c->n_sim;
+  a.do_sim = do_sim ? 1 : 0;
+  a.hist = c->hist;
+  a.hist_len = effective_hist(c->cfg);
+  a.sums = c->sums;
+  a.counts = c->counts;
+  a.dev_step = c->dev_step;
+  a.ticket = c->ticket;
+  a.status = c->status;
+  a.s_plus = c->s_plus;
+  a.s_minus = c->s_minus;
+  a.a_plus = c->a_plus;
+  a.a_minus = c->a_minus;
+  a.half_pen = c->half_pen;
+  a.tau_plus = c->cfg.tau_plus;
+  a.ntiles_x = (c->L.nx + kTileX - 1) / kTileX;
+  a.ntiles = a.ntiles_x * ((c->L.ny + kTileY - 1) / kTileY);
+  return a;
+}
+
+bool sim_due(const vplbm_ctx *c, long long step) {
+  return c->sim_every > 0 && c->n_sim > 0 && step % c->sim_every == 0;
+}
+
+vplbm_status one_step(vplbm_ctx *c, cudaStream_t s) {
+  const StepArgs a = step_args(c, c->cur, sim_due(c, c->steps));
+  VPLBM_CUDA(c, launch_step(c->cfg.dtype, !c->pre, a, c->grid, s));
+  ++c->launches;
+  c->cur = 1 - c->cur;
+  c->pre = false;
+  ++c->steps;
+  return VPLBM_OK;
+}
+
+// graph of 2 * kGraphPairs gather steps starting from buffer 0; valid when
+// SIM runs every step or never (the step kernels are then identical)
+vplbm_status ensure_graph(vplbm_ctx *c) {
+  if (c->graph) return VPLBM_OK;
+  if (!c->capture_stream)
+    VPLBM_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  VPLBM_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k) {
+    const StepArgs a = step_args(c, k & 1, c->sim_every == 1 && c->n_sim > 0);
+    e = launch_step(c->cfg.dtype, true, a, c->grid, c->capture_stream);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(c, e, "capture of the step graph");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return cuda_fail(c, e, "cudaGraphInstantiate");
+  }
+  return VPLBM_OK;
+}
+
+vplbm_status sync(vplbm_ctx *c) {
+  VPLBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VPLBM_OK;
+}
+
+vplbm_status read_status(vplbm_ctx *c, int32_t *st) {
+  VPLBM_CUDA(c, cudaMemcpyAsync(st, c->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  return sync(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+vplbm_status vplbm_workspace_bytes(const vplbm_config *cfg, size_t *bytes) {
+  if (const char *m = check_config(cfg)) return fail(nullptr, VPLBM_EINVAL, m);
+  if (!bytes) return fail(nullptr, VPLBM_EINVAL, "bytes is NULL");
+  *bytes = make_layout(*cfg).total;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_create(const vplbm_config *cfg, void *dev_workspace, size_t bytes,
+                          void *cuda_stream, vplbm_ctx **out) {
+  if (const char *m = check_config(cfg)) return fail(nullptr, VPLBM_EINVAL, m);
+  if (!out) return fail(nullptr, VPLBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!dev_workspace || ((uintptr_t)dev_workspace % kAlign) != 0)
+    return fail(nullptr, VPLBM_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  const Layout lay = make_layout(*cfg);
+  if (bytes < lay.total)
+    return fail(nullptr, VPLBM_ENOMEM, fmt("workspace of %zu bytes, %zu needed", bytes, lay.total));
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, dev_workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(nullptr, VPLBM_EINVAL, "workspace is not device memory");
+  }
+  vplbm_ctx *c = new vplbm_ctx();
+  c->cfg = *cfg;
+  c->lay = lay;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&c->device);
+  c->ws = (char *)dev_workspace;
+  c->buf[0] = c->ws + lay.buf[0];
+  c->buf[1] = c->ws + lay.buf[1];
+  c->prev[0] = (double *)(c->ws + lay.prev[0]);
+  c->prev[1] = (double *)(c->ws + lay.prev[1]);
+  c->chi = (uint8_t *)(c->ws + lay.chi);
+  c->partials = (double *)(c->ws + lay.partials);
+  c->sim_pts = (SimPoint *)(c->ws + lay.sim_pts);
+  c->sim_contrib = (double *)(c->ws + lay.sim_contrib);
+  c->sim_nodes = (int32_t *)(c->ws + lay.sim_nodes);
+  c->hist = (double *)(c->ws + lay.hist);
+  c->body = (BodyState *)(c->ws + lay.body);
+  c->sums = (double *)(c->ws + lay.sums);
+  c->counts = (long long *)(c->ws + lay.counts);
+  c->dev_step = (long long *)(c->ws + lay.dev_step);
+  c->ticket = (unsigned int *)(c->ws + lay.ticket);
+  c->status = (int32_t *)(c->ws + lay.status);
+
+  Lattice &L = c->L;
+  L.nx = cfg->nx;
+  L.ny = cfg->ny;
+  L.pitch = pitch_of(cfg->nx);
+  L.plane = (int64_t)L.pitch * L.ny;
+  for (int k = 0; k < 4; ++k) L.bc[k] = cfg->bc[k];
+  for (int a = 0; a < 9; ++a) {
+    // inlet bounce-back from a wall moving at u_in: 2 w_a rho_w (c_a.u_in) / cs2, rho_w = 1
+    const double cu = cx_of(a) * cfg->u_in[0] + cy_of(a) * cfg->u_in[1];
+    L.kin[a] = 2.0 * w_of(a) * cu * 3.0;
+  }
+  L.uc = sqrt(cfg->u_in[0] * cfg->u_in[0] + cfg->u_in[1] * cfg->u_in[1]);
+  L.bf[0] = cfg->body_force[0];
+  L.bf[1] = cfg->body_force[1];
+
+  const double tp = cfg->tau_plus;
+  const double tm = cfg->collision == VPLBM_BGK ? tp : cfg->lambda_trt / (tp - 0.5) + 0.5;
+  c->s_plus = 1.0 / tp;
+  c->s_minus = 1.0 / tm;
+  c->a_plus = 1.0 - 0.5 / tp;
+  c->a_minus = (cfg->collision == VPLBM_TRT && cfg->forcing == VPLBM_FORCING_SPLIT) ? 1.0 - 0.5 / tm
+                                                                                  : c->a_plus;
+  c->half_pen = 0.5 / cfg->eta;
+
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int per_sm = step_blocks_per_sm(cfg->dtype, true);
+  const int ntiles = ((L.nx + kTileX - 1) / kTileX) * ((L.ny + kTileY - 1) / kTileY);
+  c->grid = std::max(1, std::min({sms * per_sm, ntiles, kMaxBlocks}));
+
+  cudaError_t e = cudaMemsetAsync(c->ws, 0, lay.total, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(nullptr, e, "clearing the workspace");
+  }
+  *out = c;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_set_stream(vplbm_ctx *c, void *cuda_stream) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  c->stream = (cudaStream_t)cuda_stream;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!b) return fail(c, VPLBM_EINVAL, "body is NULL");
+  const Lattice &L = c->L;
+  BodyState bs{};
+  bs.kind = b->kind;
+  bs.xg = b->x_c;
+  bs.yg = b->y_c;
+  bs.theta = b->angle;
+  bs.ux = b->u[0];
+  bs.uy = b->u[1];
+  bs.omega = b->omega;
+  bs.length = b->length;
+  bs.thickness = b->thickness;
+  bs.pivot_frac = b->pivot_chord_frac;
+  bs.cos_a = cos(b->angle);
+  bs.sin_a = sin(b->angle);
+  bs.density_ratio = b->density_ratio;
+  bs.gx = b->gravity[0];
+  bs.gy = b->gravity[1];
+  bs.moving = b->moving;
+  bs.estimator = b->estimator;
+  std::vector<SimPoint> pts;
+  int n_sim = 0;
+  if (b->kind != VPLBM_BODY_NONE) {
+    if (b->kind != VPLBM_BODY_DISK && b->kind != VPLBM_BODY_NACA4)
+      return fail(c, VPLBM_EINVAL, "unknown body kind");
+    if (!(b->length > 0.0)) return fail(c, VPLBM_EINVAL, "body length must be > 0");
+    if (b->kind == VPLBM_BODY_NACA4) {
+      if (!(b->thickness > 0.0 && b->thickness < 0.5)) return fail(c, VPLBM_EINVAL, "bad NACA thickness");
+      if (!(b->pivot_chord_frac >= 0.0 && b->pivot_chord_frac <= 1.0))
+        return fail(c, VPLBM_EINVAL, "pivot must lie on the chord");
+      if (b->moving) return fail(c, VPLBM_EINVAL, "only a disk can move");
+    }
+    if (b->moving) {
+      if (!(b->density_ratio > 0.0)) return fail(c, VPLBM_EINVAL, "density ratio must be > 0");
+      if (b->estimator != VPLBM_MEM && b->estimator != VPLBM_SIM)
+        return fail(c, VPLBM_EINVAL, "unknown estimator");
+    }
+    n_sim = default_sim_points(*b);
+    if (n_sim > effective_max_sim(c->cfg))
+      return fail(c, VPLBM_EINVAL, fmt("%d SIM points exceed the capacity %d", n_sim, effective_max_sim(c->cfg)));
+    if (!build_polygon(*b, n_sim, pts)) return fail(c, VPLBM_EINVAL, "bad SIM point count for this body");
+    // the body (its polygon, with one node of margin) must lie inside the lattice
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (const SimPoint &p : pts) {
+      x0 = std::min(x0, b->x_c + p.dx - 0.5 * p.s);
+      x1 = std::max(x1, b->x_c + p.dx + 0.5 * p.s);
+      y0 = std::min(y0, b->y_c + p.dy - 0.5 * p.s);
+      y1 = std::max(y1, b->y_c + p.dy + 0.5 * p.s);
+    }
+    if (!(x0 >= 0.0 && y0 >= 0.0 && x1 <= L.nx - 1.0 && y1 <= L.ny - 1.0))
+      return fail(c, VPLBM_EINVAL, "body does not fit in the lattice");
+  }
+  c->body_cfg = *b;
+  c->body_host = bs;
+  c->n_sim = n_sim;
+  c->sim_every = (b->moving && b->estimator == VPLBM_SIM) ? 1 : c->cfg.sim_every;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  cudaStream_t s = c->stream;
+  VPLBM_CUDA(c, cudaMemcpyAsync(c->body, &c->body_host, sizeof(BodyState), cudaMemcpyHostToDevice, s));
+  if (n_sim > 0)
+    VPLBM_CUDA(c, cudaMemcpyAsync(c->sim_pts, pts.data(), n_sim * sizeof(SimPoint), cudaMemcpyHostToDevice, s));
+  VPLBM_CUDA(c, cudaMemsetAsync(c->chi, 0, (size_t)L.plane, s));
+  if (b->kind != VPLBM_BODY_NONE) {
+    VPLBM_CUDA(c, launch_raster(L, c->body, c->chi, 0, 0, L.nx - 1, L.ny - 1, s));
+    VPLBM_CUDA(c, launch_interface(L, c->chi, 0, 0, L.nx - 1, L.ny - 1, s));
+    c->launches += 2;
+  }
+  VPLBM_CUDA(c, launch_init(c->cfg.dtype, L, c->body, c->chi, c->buf[0], c->cfg.u_in[0], c->cfg.u_in[1], s));
+  ++c->launches;
+  // histories, sums, counters, status
+  VPLBM_CUDA(c, cudaMemsetAsync(c->ws + c->lay.hist, 0, c->lay.body - c->lay.hist, s));
+  VPLBM_CUDA(c, cudaMemsetAsync(c->ws + c->lay.sums, 0, c->lay.total - c->lay.sums, s));
+  VPLBM_CUDA(c, cudaMemsetAsync(c->prev[0], 0, 3 * (size_t)L.ny * sizeof(double), s));
+  VPLBM_CUDA(c, cudaMemsetAsync(c->prev[1], 0, 3 * (size_t)L.ny * sizeof(double), s));
+  VPLBM_CUDA(c, cudaGetLastError());
+  c->cur = 0;
+  c->pre = true;
+  c->steps = 0;
+  c->has_body = true;
+  return sync(c);
+}
+
+vplbm_status vplbm_step(vplbm_ctx *c, int32_t nsteps) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return fail(c, VPLBM_EINVAL, "nsteps must be >= 0");
+  if (!c->has_body) return fail(c, VPLBM_ESTATE, "no body placed (vplbm_set_body)");
+  cudaStream_t s = c->stream;
+  int left = nsteps;
+  const bool graphable = s != nullptr && (c->sim_every <= 1);
+  while (left > 0) {
+    if (graphable && !c->pre && c->cur == 0 && left >= 2 * kGraphPairs) {
+      if (vplbm_status st = ensure_graph(c)) return st;
+      VPLBM_CUDA(c, cudaGraphLaunch(c->graph, s));
+      c->launches += 2 * kGraphPairs;
+      c->steps += 2 * kGraphPairs;
+      left -= 2 * kGraphPairs;
+      continue;
+    }
+    if (vplbm_status st = one_step(c, s)) return st;
+    --left;
+  }
+  return VPLBM_OK;
+}
+
+static vplbm_status read_hist_entry(vplbm_ctx *c, long long step, double out[6]) {
+  const int len = effective_hist(c->cfg);
+  VPLBM_CUDA(c, cudaMemcpyAsync(out, c->hist + 6 * (step % len), 6 * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+  return sync(c);
+}
+
+vplbm_status vplbm_force_mem(vplbm_ctx *c, double F[2], double *T) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!F || !T) return fail(c, VPLBM_EINVAL, "NULL output");
+  if (c->steps == 0) return fail(c, VPLBM_ESTATE, "no step taken");
+  double e[6];
+  if (vplbm_status st = read_hist_entry(c, c->steps - 1, e)) return st;
+  int32_t status = 0;
+  if (vplbm_status st = read_status(c, &status)) return st;
+  F[0] = e[0];
+  F[1] = e[1];
+  *T = e[2];
+  if (status & kStatusUnstable) return fail(c, VPLBM_EUNSTABLE, "non-finite or non-positive density");
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_force_sim(vplbm_ctx *c, double F[2], double *T) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!F || !T) return fail(c, VPLBM_EINVAL, "NULL output");
+  if (c->sim_every <= 0 || c->n_sim <= 0 || c->steps == 0) return fail(c, VPLBM_ESTATE, "SIM not evaluated");
+  const long long last = (c->steps - 1) / c->sim_every * c->sim_every;
+  if (c->steps - 1 - last >= effective_hist(c->cfg)) return fail(c, VPLBM_ESTATE, "SIM entry left the history");
+  double e[6];
+  if (vplbm_status st = read_hist_entry(c, last, e)) return st;
+  int32_t status = 0;
+  if (vplbm_status st = read_status(c, &status)) return st;
+  F[0] = e[3];
+  F[1] = e[4];
+  *T = e[5];
+  if (status & kStatusUnstable) return fail(c, VPLBM_EUNSTABLE, "non-finite or non-positive density");
+  if (status & kStatusSimMissing) return fail(c, VPLBM_ESTATE, "a SIM point found no fluid node");
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_forces_async(vplbm_ctx *c, double *out) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!out) return fail(c, VPLBM_EINVAL, "NULL output");
+  if (c->steps == 0) return fail(c, VPLBM_ESTATE, "no step taken");
+  const int len = effective_hist(c->cfg);
+  VPLBM_CUDA(c, cudaMemcpyAsync(out, c->hist + 6 * ((c->steps - 1) % len), 6 * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_force_history(vplbm_ctx *c, int32_t estimator, int32_t count, double *out) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  const int len = effective_hist(c->cfg);
+  if (!out || count < 0 || count > len || count > c->steps)
+    return fail(c, VPLBM_EINVAL, "bad history request");
+  if (estimator != VPLBM_MEM && estimator != VPLBM_SIM) return fail(c, VPLBM_EINVAL, "unknown estimator");
+  std::vector<double> all((size_t)len * 6);
+  VPLBM_CUDA(c, cudaMemcpyAsync(all.data(), c->hist, all.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (vplbm_status st = sync(c)) return st;
+  const int off = estimator == VPLBM_SIM ? 3 : 0;
+  for (int k = 0; k < count; ++k) {
+    const long long step = c->steps - count + k;
+    for (int q = 0; q < 3; ++q) out[3 * k + q] = all[6 * (step % len) + off + q];
+  }
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_force_sums(vplbm_ctx *c, double sums[6], int64_t n[2]) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!sums || !n) return fail(c, VPLBM_EINVAL, "NULL output");
+  long long cnt[2];
+  VPLBM_CUDA(c, cudaMemcpyAsync(sums, c->sums, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  VPLBM_CUDA(c, cudaMemcpyAsync(cnt, c->counts, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+  if (vplbm_status st = sync(c)) return st;
+  n[0] = cnt[0];
+  n[1] = cnt[1];
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_reset_sums(vplbm_ctx *c) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  VPLBM_CUDA(c, cudaMemsetAsync(c->sums, 0, 6 * sizeof(double), c->stream));
+  VPLBM_CUDA(c, cudaMemsetAsync(c->counts, 0, 2 * sizeof(long long), c->stream));
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_step_count(vplbm_ctx *c, int64_t *n) {
+  if (!c || !n) return fail(c, VPLBM_EINVAL, "NULL argument");
+  *n = c->steps;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_get_f(vplbm_ctx *c, double *f_dev) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!f_dev) return fail(c, VPLBM_EINVAL, "f_dev is NULL");
+  if (!c->has_body) return fail(c, VPLBM_ESTATE, "no state yet");
+  VPLBM_CUDA(c, launch_get_f(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], f_dev, c->stream));
+  ++c->launches;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_get_fields(vplbm_ctx *c, double *rho, double *ux, double *uy) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!rho || !ux || !uy) return fail(c, VPLBM_EINVAL, "NULL output");
+  if (!c->has_body) return fail(c, VPLBM_ESTATE, "no state yet");
+  VPLBM_CUDA(c, launch_get_fields(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], c->chi,
+                                  c->body, c->half_pen, rho, ux, uy, c->stream));
+  ++c->launches;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_set_state(vplbm_ctx *c, const double *f_dev, const double *prev_dev,
+                             int32_t post_collision) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!f_dev) return fail(c, VPLBM_EINVAL, "f_dev is NULL");
+  if (!c->has_body) return fail(c, VPLBM_ESTATE, "place a body first");
+  if (post_collision && c->cfg.bc[1] == VPLBM_OUTLET_CONVECTIVE && !prev_dev)
+    return fail(c, VPLBM_EINVAL, "the convective outlet needs the previous pre-collision field");
+  VPLBM_CUDA(c, launch_set_state(c->cfg.dtype, c->L, f_dev, c->buf[c->cur], c->stream));
+  ++c->launches;
+  if (post_collision && prev_dev) {
+    VPLBM_CUDA(c, launch_set_prev(c->L, prev_dev, c->prev[c->cur], c->stream));
+    ++c->launches;
+  }
+  c->pre = post_collision == 0;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_get_mask(vplbm_ctx *c, uint8_t *chi_dev) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!chi_dev) return fail(c, VPLBM_EINVAL, "chi_dev is NULL");
+  VPLBM_CUDA(c, launch_get_mask(c->L, c->chi, chi_dev, c->stream));
+  ++c->launches;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_get_body(vplbm_ctx *c, double state[6]) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!state) return fail(c, VPLBM_EINVAL, "NULL output");
+  BodyState b;
+  VPLBM_CUDA(c, cudaMemcpyAsync(&b, c->body, sizeof b, cudaMemcpyDeviceToHost, c->stream));
+  if (vplbm_status st = sync(c)) return st;
+  state[0] = b.xg;
+  state[1] = b.yg;
+  state[2] = b.theta;
+  state[3] = b.ux;
+  state[4] = b.uy;
+  state[5] = b.omega;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_get_sim_nodes(vplbm_ctx *c, int32_t *nodes, int32_t capacity, int32_t *n) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!n || (capacity > 0 && !nodes)) return fail(c, VPLBM_EINVAL, "NULL output");
+  *n = c->n_sim;
+  if (capacity < c->n_sim) return fail(c, VPLBM_EINVAL, "capacity below the SIM point count");
+  if (c->n_sim > 0) {
+    VPLBM_CUDA(c, cudaMemcpyAsync(nodes, c->sim_nodes, c->n_sim * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+  }
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_check(vplbm_ctx *c) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  int32_t status = 0;
+  if (vplbm_status st = read_status(c, &status)) return st;
+  if (status & kStatusUnstable) return fail(c, VPLBM_EUNSTABLE, "non-finite or non-positive density");
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_launch_count(vplbm_ctx *c, int64_t *n) {
+  if (!c || !n) return fail(c, VPLBM_EINVAL, "NULL argument");
+  *n = c->launches;
+  return VPLBM_OK;
+}
+
+void vplbm_destroy(vplbm_ctx *c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  delete c;
+}
+
+const char *vplbm_last_error(const vplbm_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

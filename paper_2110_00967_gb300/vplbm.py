@@ -1,0 +1,397 @@
+"""Python binding of the VP-LBM C ABI (include/vplbm.h).
+
+The module-level functions carry the C names and only marshal arguments; every
+step of the method runs in the CUDA library.  PyTorch provides the device
+workspace, the stream and the device buffers of the field read-back calls.
+`Lattice` bundles one context with its workspace.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# enums (values of include/vplbm.h)
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
+F64, F32, F16_OFS, BF16_OFS = range(4)
+BGK, TRT = 0, 1
+FORCING_PAPER, FORCING_SPLIT = 0, 1
+PERIODIC, INLET_BB, OUTLET_CONVECTIVE, SYMMETRY, NOSLIP_BB = range(5)
+BODY_NONE, BODY_DISK, BODY_NACA4 = range(3)
+MEM, SIM = 0, 1
+
+_STATUS = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
+           EUNSTABLE: "EUNSTABLE", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
+
+
+class VplbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vplbm_config(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("dtype", C.c_int32), ("collision", C.c_int32),
+        ("forcing", C.c_int32), ("bc", C.c_int32 * 4), ("sim_every", C.c_int32),
+        ("max_sim_points", C.c_int32), ("history_len", C.c_int32),
+        ("tau_plus", C.c_double), ("lambda_trt", C.c_double), ("eta", C.c_double),
+        ("u_in", C.c_double * 2), ("body_force", C.c_double * 2),
+    ]
+
+
+class vplbm_body(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("moving", C.c_int32), ("n_sim_points", C.c_int32),
+        ("estimator", C.c_int32), ("length", C.c_double), ("thickness", C.c_double),
+        ("x_c", C.c_double), ("y_c", C.c_double), ("angle", C.c_double),
+        ("pivot_chord_frac", C.c_double), ("u", C.c_double * 2), ("omega", C.c_double),
+        ("density_ratio", C.c_double), ("gravity", C.c_double * 2),
+    ]
+
+
+def config(nx, ny, dtype=F32, collision=TRT, forcing=FORCING_PAPER,
+           bc=(PERIODIC, PERIODIC, PERIODIC, PERIODIC), sim_every=1, max_sim_points=0,
+           history_len=0, tau_plus=0.8, lambda_trt=1.0 / 6.0, eta=1e-6, u_in=(0.0, 0.0),
+           body_force=(0.0, 0.0)) -> vplbm_config:
+    c = vplbm_config()
+    c.nx, c.ny, c.dtype, c.collision, c.forcing = nx, ny, dtype, collision, forcing
+    for k in range(4):
+        c.bc[k] = bc[k]
+    c.sim_every, c.max_sim_points, c.history_len = sim_every, max_sim_points, history_len
+    c.tau_plus, c.lambda_trt, c.eta = tau_plus, lambda_trt, eta
+    c.u_in[0], c.u_in[1] = u_in
+    c.body_force[0], c.body_force[1] = body_force
+    return c
+
+
+def body(kind=BODY_NONE, length=0.0, thickness=0.12, x_c=0.0, y_c=0.0, angle=0.0,
+         pivot_chord_frac=0.25, u=(0.0, 0.0), omega=0.0, moving=0, density_ratio=1.0,
+         gravity=(0.0, 0.0), n_sim_points=0, estimator=MEM) -> vplbm_body:
+    b = vplbm_body()
+    b.kind, b.moving, b.n_sim_points, b.estimator = kind, moving, n_sim_points, estimator
+    b.length, b.thickness, b.x_c, b.y_c, b.angle = length, thickness, x_c, y_c, angle
+    b.pivot_chord_frac = pivot_chord_frac
+    b.u[0], b.u[1] = u
+    b.omega, b.density_ratio = omega, density_ratio
+    b.gravity[0], b.gravity[1] = gravity
+    return b
+
+
+_lib = None
+
+# (name, argtypes, restype) of every entry point of include/vplbm.h
+_P = C.POINTER
+_vp = C.c_void_p
+_SIGS = [
+    ("vplbm_workspace_bytes", [_P(vplbm_config), _P(C.c_size_t)], C.c_int),
+    ("vplbm_create", [_P(vplbm_config), _vp, C.c_size_t, _vp, _P(_vp)], C.c_int),
+    ("vplbm_set_stream", [_vp, _vp], C.c_int),
+    ("vplbm_set_body", [_vp, _P(vplbm_body)], C.c_int),
+    ("vplbm_step", [_vp, C.c_int32], C.c_int),
+    ("vplbm_force_mem", [_vp, _P(C.c_double), _P(C.c_double)], C.c_int),
+    ("vplbm_force_sim", [_vp, _P(C.c_double), _P(C.c_double)], C.c_int),
+    ("vplbm_forces_async", [_vp, _vp], C.c_int),
+    ("vplbm_force_history", [_vp, C.c_int32, C.c_int32, _P(C.c_double)], C.c_int),
+    ("vplbm_force_sums", [_vp, _P(C.c_double), _P(C.c_int64)], C.c_int),
+    ("vplbm_reset_sums", [_vp], C.c_int),
+    ("vplbm_step_count", [_vp, _P(C.c_int64)], C.c_int),
+    ("vplbm_get_f", [_vp, _vp], C.c_int),
+    ("vplbm_get_fields", [_vp, _vp, _vp, _vp], C.c_int),
+    ("vplbm_set_state", [_vp, _vp, _vp, C.c_int32], C.c_int),
+    ("vplbm_get_mask", [_vp, _vp], C.c_int),
+    ("vplbm_get_body", [_vp, _P(C.c_double)], C.c_int),
+    ("vplbm_get_sim_nodes", [_vp, _P(C.c_int32), C.c_int32, _P(C.c_int32)], C.c_int),
+    ("vplbm_check", [_vp], C.c_int),
+    ("vplbm_launch_count", [_vp, _P(C.c_int64)], C.c_int),
+    ("vplbm_destroy", [_vp], None),
+    ("vplbm_last_error", [_vp], C.c_char_p),
+]
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib():
+    """Loads libvplbm.so (building it when sources are newer).  Raises when the
+    library cannot be built or loaded: there is no fallback path."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = C.CDLL(path)
+        for name, args, res in _SIGS:
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st, ctx=None):
+    if st != OK:
+        msg = lib().vplbm_last_error(ctx)
+        raise VplbmError(st, msg.decode() if msg else "")
+
+
+def _dptr(t) -> int:
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+def vplbm_workspace_bytes(cfg: vplbm_config) -> int:
+    n = C.c_size_t()
+    _check(lib().vplbm_workspace_bytes(C.byref(cfg), C.byref(n)))
+    return n.value
+
+
+def vplbm_create(cfg: vplbm_config, workspace_ptr: int, nbytes: int, stream: int):
+    ctx = _vp()
+    _check(lib().vplbm_create(C.byref(cfg), workspace_ptr, nbytes, stream, C.byref(ctx)))
+    return ctx
+
+
+def vplbm_set_stream(ctx, stream: int):
+    _check(lib().vplbm_set_stream(ctx, stream), ctx)
+
+
+def vplbm_set_body(ctx, b: vplbm_body):
+    _check(lib().vplbm_set_body(ctx, C.byref(b)), ctx)
+
+
+def vplbm_step(ctx, nsteps: int):
+    _check(lib().vplbm_step(ctx, nsteps), ctx)
+
+
+def _force(fn, ctx):
+    F = (C.c_double * 2)()
+    T = C.c_double()
+    _check(fn(ctx, F, C.byref(T)), ctx)
+    return np.array([F[0], F[1], T.value])
+
+
+def vplbm_force_mem(ctx):
+    return _force(lib().vplbm_force_mem, ctx)
+
+
+def vplbm_force_sim(ctx):
+    return _force(lib().vplbm_force_sim, ctx)
+
+
+def vplbm_forces_async(ctx, host_ptr: int):
+    _check(lib().vplbm_forces_async(ctx, host_ptr), ctx)
+
+
+def vplbm_force_history(ctx, estimator: int, count: int):
+    out = np.zeros((count, 3))
+    _check(lib().vplbm_force_history(ctx, estimator, count,
+                                     out.ctypes.data_as(_P(C.c_double))), ctx)
+    return out
+
+
+def vplbm_force_sums(ctx):
+    s = np.zeros(6)
+    n = np.zeros(2, np.int64)
+    _check(lib().vplbm_force_sums(ctx, s.ctypes.data_as(_P(C.c_double)),
+                                  n.ctypes.data_as(_P(C.c_int64))), ctx)
+    return s, n
+
+
+def vplbm_reset_sums(ctx):
+    _check(lib().vplbm_reset_sums(ctx), ctx)
+
+
+def vplbm_step_count(ctx) -> int:
+    n = C.c_int64()
+    _check(lib().vplbm_step_count(ctx, C.byref(n)), ctx)
+    return n.value
+
+
+def vplbm_get_f(ctx, f_dev_ptr: int):
+    _check(lib().vplbm_get_f(ctx, f_dev_ptr), ctx)
+
+
+def vplbm_get_fields(ctx, rho_ptr: int, ux_ptr: int, uy_ptr: int):
+    _check(lib().vplbm_get_fields(ctx, rho_ptr, ux_ptr, uy_ptr), ctx)
+
+
+def vplbm_set_state(ctx, f_dev_ptr: int, prev_dev_ptr, post_collision: int):
+    _check(lib().vplbm_set_state(ctx, f_dev_ptr, prev_dev_ptr, post_collision), ctx)
+
+
+def vplbm_get_mask(ctx, chi_dev_ptr: int):
+    _check(lib().vplbm_get_mask(ctx, chi_dev_ptr), ctx)
+
+
+def vplbm_get_body(ctx):
+    s = (C.c_double * 6)()
+    _check(lib().vplbm_get_body(ctx, s), ctx)
+    return np.array(list(s))
+
+
+def vplbm_get_sim_nodes(ctx, capacity: int):
+    out = np.zeros(max(capacity, 1), np.int32)
+    n = C.c_int32()
+    _check(lib().vplbm_get_sim_nodes(ctx, out.ctypes.data_as(_P(C.c_int32)), capacity,
+                                     C.byref(n)), ctx)
+    return out[:n.value]
+
+
+def vplbm_check(ctx):
+    _check(lib().vplbm_check(ctx), ctx)
+
+
+def vplbm_launch_count(ctx) -> int:
+    n = C.c_int64()
+    _check(lib().vplbm_launch_count(ctx, C.byref(n)), ctx)
+    return n.value
+
+
+def vplbm_destroy(ctx):
+    lib().vplbm_destroy(ctx)
+
+
+def vplbm_last_error(ctx=None) -> str:
+    m = lib().vplbm_last_error(ctx)
+    return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------
+# one lattice with its workspace
+# ---------------------------------------------------------------------------
+class Lattice:
+    """A lattice in a PyTorch-allocated device workspace."""
+
+    def __init__(self, cfg: vplbm_config, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.nbytes = vplbm_workspace_bytes(cfg)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            self._ws_ptr = (base + 255) // 256 * 256
+            self.ctx = vplbm_create(cfg, self._ws_ptr, self.nbytes, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            vplbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        vplbm_set_stream(self.ctx, stream.cuda_stream)
+
+    def set_body(self, b: vplbm_body):
+        self.body_cfg = b
+        vplbm_set_body(self.ctx, b)
+
+    def step(self, n: int = 1):
+        vplbm_step(self.ctx, n)
+
+    def force_mem(self):
+        return vplbm_force_mem(self.ctx)
+
+    def force_sim(self):
+        return vplbm_force_sim(self.ctx)
+
+    def history(self, estimator: int, count: int):
+        return vplbm_force_history(self.ctx, estimator, count)
+
+    def sums(self):
+        return vplbm_force_sums(self.ctx)
+
+    def reset_sums(self):
+        vplbm_reset_sums(self.ctx)
+
+    @property
+    def steps(self) -> int:
+        return vplbm_step_count(self.ctx)
+
+    def _empty(self, shape, dtype):
+        return self.torch.empty(shape, dtype=dtype, device=self.device)
+
+    def get_f(self) -> np.ndarray:
+        out = self._empty((9, self.cfg.ny, self.cfg.nx), self.torch.float64)
+        with self.torch.cuda.stream(self.stream):
+            vplbm_get_f(self.ctx, _dptr(out))
+            return out.cpu().numpy()
+
+    def get_fields(self):
+        t = self.torch
+        rho, ux, uy = (self._empty((self.cfg.ny, self.cfg.nx), t.float64) for _ in range(3))
+        with t.cuda.stream(self.stream):
+            vplbm_get_fields(self.ctx, _dptr(rho), _dptr(ux), _dptr(uy))
+            return rho.cpu().numpy(), ux.cpu().numpy(), uy.cpu().numpy()
+
+    def set_state(self, f: np.ndarray, prev: np.ndarray | None = None, post_collision=False):
+        t = self.torch
+        with t.cuda.stream(self.stream):
+            fd = t.as_tensor(np.ascontiguousarray(f, np.float64)).to(self.device)
+            pd = None if prev is None else t.as_tensor(np.ascontiguousarray(prev, np.float64)).to(self.device)
+            vplbm_set_state(self.ctx, _dptr(fd), None if pd is None else _dptr(pd),
+                            1 if post_collision else 0)
+            self.stream.synchronize()
+
+    def get_mask(self) -> np.ndarray:
+        out = self._empty((self.cfg.ny, self.cfg.nx), self.torch.uint8)
+        with self.torch.cuda.stream(self.stream):
+            vplbm_get_mask(self.ctx, _dptr(out))
+            return out.cpu().numpy()
+
+    def get_body(self):
+        return vplbm_get_body(self.ctx)
+
+    def sim_nodes(self):
+        n = 8192 if self.cfg.max_sim_points == 0 else self.cfg.max_sim_points
+        return vplbm_get_sim_nodes(self.ctx, n)
+
+    def check(self):
+        vplbm_check(self.ctx)
+
+    @property
+    def launches(self) -> int:
+        return vplbm_launch_count(self.ctx)
+
+
+# ---------------------------------------------------------------------------
+# workloads -> ABI structures
+# ---------------------------------------------------------------------------
+_DTYPES = {"f64": F64, "f32": F32, "f16": F16_OFS, "bf16": BF16_OFS}
+_BCS = {"periodic": PERIODIC, "inlet": INLET_BB, "outlet": OUTLET_CONVECTIVE,
+        "symmetry": SYMMETRY, "noslip": NOSLIP_BB}
+_KINDS = {"none": BODY_NONE, "disk": BODY_DISK, "naca": BODY_NACA4}
+
+
+def config_of(w, dtype: str | None = None, **over) -> vplbm_config:
+    kw = dict(nx=w.nx, ny=w.ny, dtype=_DTYPES[dtype or w.dtype],
+              collision=BGK if w.collision == "bgk" else TRT,
+              forcing=FORCING_PAPER if w.forcing == "paper" else FORCING_SPLIT,
+              bc=tuple(_BCS[b] for b in w.bc), sim_every=w.sim_every, tau_plus=w.tau_plus,
+              lambda_trt=w.lambda_trt, eta=w.eta, u_in=w.u_in, body_force=w.body_force)
+    kw.update(over)
+    return config(**kw)
+
+
+def body_of(w) -> vplbm_body:
+    b = w.body
+    return body(kind=_KINDS[b.kind], length=b.length, thickness=b.thickness, x_c=b.x_c,
+                y_c=b.y_c, angle=b.angle, pivot_chord_frac=b.pivot_chord_frac,
+                moving=1 if b.moving else 0, density_ratio=b.density_ratio,
+                gravity=b.gravity, n_sim_points=b.n_sim_points,
+                estimator=SIM if b.estimator == "sim" else MEM)

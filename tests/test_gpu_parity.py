@@ -1,0 +1,361 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle.
+
+Bars: bit-exact for streaming moves, masks and SIM sampling nodes; 1e-12
+relative for the FP64 path; 1e-5 relative on fields after 1000 FP32 steps
+(L-inf error over L-inf of the oracle field, for rho - 1, u_x, u_y); Cd/Cl
+within 1e-3 of the FP64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2110_00967_gb300 import vplbm as V
+from paper_2110_00967_gb300 import workloads as W
+from tests.helpers import oracle_setup
+
+pytestmark = pytest.mark.gpu
+
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "the GPU tests need a CUDA device"
+    V.lib()
+    yield
+
+
+def lattice(w, dtype=None, **over):
+    lat = V.Lattice(V.config_of(w, dtype=dtype, **over))
+    lat.set_body(V.body_of(w))
+    return lat
+
+
+def rel_linf(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def round_storage(h, dtype):
+    """Round-to-nearest-even of FP64 offsets to the storage type, in numpy."""
+    if dtype == "f64":
+        return h.copy()
+    if dtype == "f32":
+        return h.astype(np.float32).astype(np.float64)
+    if dtype == "f16":
+        return h.astype(np.float16).astype(np.float64)
+    m, e = np.frexp(h)  # bfloat16: 8 significant bits, float32 exponent range
+    return np.ldexp(np.round(m * 256.0) / 256.0, e)
+
+
+def small_case(bc, dtype="f64", nx=37, ny=21, body="disk", collision="trt", forcing="paper",
+               steps=30, tau=0.6, u=(0.04, 0.01), body_force=(0.0, 0.0)):
+    if body == "disk":
+        b = W.Body("disk", length=8.0, x_c=15.3, y_c=10.2)
+    elif body == "naca":
+        b = W.Body("naca", length=20.0, x_c=12.0, y_c=10.0, angle_deg=12.0, n_sim_points=41)
+    else:
+        b = W.Body("none")
+    return W.Workload(name="small", nx=nx, ny=ny, dtype=dtype, collision=collision,
+                      tau_plus=tau, u_in=u, bc=bc, body=b, steps=steps, forcing=forcing,
+                      body_force=body_force)
+
+
+# ---------------------------------------------------------------------------
+# exact index and data-movement work
+# ---------------------------------------------------------------------------
+MOVE_BCS = [
+    ("periodic", "periodic", "periodic", "periodic"),
+    ("periodic", "periodic", "noslip", "noslip"),
+    ("noslip", "noslip", "symmetry", "symmetry"),
+    ("noslip", "noslip", "noslip", "noslip"),
+]
+
+
+@pytest.mark.parametrize("bc", MOVE_BCS)
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("shape", [(37, 21), (131, 5), (256, 3)])
+def test_streaming_moves_are_bit_exact(bc, dtype, shape):
+    """Pull streaming with periodic, bounce-back and specular sides moves the
+    stored values: the streamed field equals the oracle's streaming of the same
+    stored values bit for bit (ragged tiles: widths 37, 131 around the 128-wide tile)."""
+    nx, ny = shape
+    w = small_case(bc, dtype=dtype, nx=nx, ny=ny, body="none")
+    lat = lattice(w)
+    ft = W.random_field(7, (9, ny, nx))
+    stored = round_storage(ft - W9[:, None, None], dtype) + W9[:, None, None]
+    lat.set_state(ft, ft, post_collision=True)
+    got = lat.get_f()
+    cfg, _, _, _, _ = oracle_setup(w)
+    ref = o.stream(cfg, stored, stored)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_inlet_and_outlet_streaming(dtype):
+    """Inlet bounce-back adds 2 w rho_w c.u_in / cs2; the convective outlet mixes
+    the previous outlet value with the inner neighbour (round-off only)."""
+    w = small_case(("inlet", "outlet", "symmetry", "symmetry"), dtype=dtype, body="none",
+                   nx=140, ny=9)
+    lat = lattice(w)
+    ft = W.random_field(8, (9, w.ny, w.nx))
+    prev = W.random_field(9, (9, w.ny, w.nx))
+    lat.set_state(ft, prev, post_collision=True)
+    got = lat.get_f()
+    cfg, _, _, _, _ = oracle_setup(w)
+    eps = 1e-15 if dtype == "f64" else 1e-7
+    # the oracle sees the stored (rounded) populations; the outlet column is kept in FP64
+    ft = round_storage(ft - W9[:, None, None], dtype) + W9[:, None, None]
+    ref = o.stream(cfg, ft, prev)
+    assert np.abs(got - ref).max() < 4 * eps
+
+
+@pytest.mark.parametrize("alpha", [0.0, 5.0, 13.7, 20.0, -8.0])
+def test_naca_mask_bit_exact(alpha):
+    w = W.naca(alpha, nx=1024, ny=512)
+    lat = lattice(w)
+    _, _, chi, _, _ = oracle_setup(w)
+    assert np.array_equal(lat.get_mask(), chi)
+
+
+@pytest.mark.parametrize("xc,yc,d", [(64.0, 64.0, 20.0), (100.37, 41.5, 33.0), (30.0, 30.5, 7.0)])
+def test_disk_mask_bit_exact(xc, yc, d):
+    w = W.disk_channel().with_(body=W.Body("disk", length=d, x_c=xc, y_c=yc))
+    lat = lattice(w)
+    _, _, chi, _, _ = oracle_setup(w)
+    assert np.array_equal(lat.get_mask(), chi)
+
+
+@pytest.mark.parametrize("w", [W.disk_channel(), W.naca(0.0, nx=512, ny=256),
+                               W.naca(15.0, nx=512, ny=256)], ids=["disk", "naca0", "naca15"])
+def test_sim_sampling_nodes_bit_exact(w):
+    lat = lattice(w)
+    lat.step(1)
+    cfg, body, chi, f, pts = oracle_setup(w)
+    _, nodes, missing = o.sim(cfg, body, chi, f, pts)
+    assert missing == 0
+    assert np.array_equal(lat.sim_nodes(), nodes)
+
+
+# ---------------------------------------------------------------------------
+# FP64 path: 1e-12 relative
+# ---------------------------------------------------------------------------
+def test_disk_channel_fp64_full_run():
+    """The 256 x 128 disk channel, BGK, FP64, all 2000 steps: per-step MEM and
+    SIM forces and the final field within 1e-12 relative of the oracle."""
+    w = W.disk_channel()
+    lat = lattice(w, history_len=2048)
+    lat.step(w.steps)
+    cfg, body, chi, f, pts = oracle_setup(w)
+    mh, sh, _, bad = o.run(cfg, body, f, chi, w.steps, sim_pts=pts)
+    assert bad == 0
+    gm, gs = lat.history(V.MEM, w.steps), lat.history(V.SIM, w.steps)
+    scale_m = np.abs(mh[:, 0]).max()
+    scale_s = np.abs(sh[:, 0]).max()
+    assert np.abs(gm - mh).max() <= 1e-12 * scale_m
+    assert np.abs(gs - sh).max() <= 1e-12 * scale_s
+    assert rel_linf(lat.get_f(), f) <= 1e-12
+    # the single-step read-back agrees with the history
+    np.testing.assert_array_equal(lat.force_mem(), gm[-1])
+    np.testing.assert_array_equal(lat.force_sim(), gs[-1])
+    # drag coefficients of the two estimators, 2F / (rho U^2 D)
+    cd_m = 2 * gm[-1, 0] / (0.05 ** 2 * 20.0)
+    cd_s = 2 * gs[-1, 0] / (0.05 ** 2 * 20.0)
+    assert abs(cd_m - 2 * mh[-1, 0] / (0.05 ** 2 * 20.0)) < 1e-12 * abs(cd_m)
+    assert cd_m > 0 and cd_s > 0
+
+
+EDGE_CASES = [
+    dict(bc=("inlet", "outlet", "symmetry", "symmetry"), body="naca"),
+    dict(bc=("inlet", "outlet", "periodic", "periodic"), body="disk", collision="bgk"),
+    dict(bc=("inlet", "outlet", "noslip", "noslip"), body="disk", forcing="split"),
+    dict(bc=("periodic", "periodic", "noslip", "noslip"), body="none", body_force=(1e-5, 0.0)),
+    dict(bc=("periodic", "periodic", "periodic", "periodic"), body="disk", body_force=(2e-6, -1e-6)),
+    dict(bc=("noslip", "noslip", "noslip", "noslip"), body="disk", u=(0.0, 0.0), body_force=(0, -1e-5)),
+    dict(bc=("inlet", "outlet", "symmetry", "noslip"), body="disk", nx=130, ny=4),
+    dict(bc=("inlet", "noslip", "symmetry", "symmetry"), body="disk", nx=3, ny=3),
+]
+
+
+@pytest.mark.parametrize("case", EDGE_CASES, ids=[str(i) for i in range(len(EDGE_CASES))])
+def test_fp64_small_cases(case):
+    case = dict(case)
+    body = case.pop("body")
+    nx, ny = case.pop("nx", 37), case.pop("ny", 21)
+    if min(nx, ny) < 12:
+        body = "none"
+    w = small_case(dtype="f64", nx=nx, ny=ny, body=body, **case)
+    lat = lattice(w)
+    lat.step(w.steps)
+    cfg, ob, chi, f, pts = oracle_setup(w)
+    mh, sh, _, bad = o.run(cfg, ob, f, chi, w.steps, sim_pts=pts)
+    assert rel_linf(lat.get_f(), f) <= 1e-12
+    if body != "none":
+        gm = lat.history(V.MEM, w.steps)
+        gs = lat.history(V.SIM, w.steps)
+        assert np.abs(gm - mh).max() <= 1e-12 * max(np.abs(mh).max(), 1e-300)
+        if bad == 0:
+            assert np.abs(gs - sh).max() <= 1e-12 * max(np.abs(sh).max(), 1e-300)
+
+
+def test_moving_disk_fp64_trajectory():
+    """A disk released under gravity in a closed box (Eqs. dep1, theta2 each
+    step, chi re-rasterised): trajectory, forces and the final mask match."""
+    for est in ("mem", "sim"):
+        w = W.Workload(name="fall", nx=48, ny=96, dtype="f64", collision="trt", tau_plus=0.6,
+                       u_in=(0.0, 0.0), bc=("noslip",) * 4,
+                       body=W.Body("disk", length=12.0, x_c=20.3, y_c=70.0, moving=True,
+                                   density_ratio=1.5, gravity=(0.0, -2e-4), estimator=est),
+                       steps=150)
+        lat = lattice(w)
+        lat.step(w.steps)
+        cfg, ob, chi, f, pts = oracle_setup(w)
+        mh, sh, bh, bad = o.run(cfg, ob, f, chi, w.steps, estimator=1 if est == "sim" else 0,
+                                sim_pts=pts)
+        assert bad == 0
+        got = lat.get_body()
+        ref = bh[-1]
+        assert abs(got[1] - ref[1]) < 1e-10 * abs(ref[1])
+        assert abs(got[4] - ref[4]) <= 1e-9 * abs(ref[4])
+        assert got[1] < 70.0 - 1.0  # it fell more than a cell
+        assert np.array_equal(lat.get_mask(), chi)
+        assert rel_linf(lat.get_f(), f) <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# FP32 and 16-bit storage against the FP64 oracle
+# ---------------------------------------------------------------------------
+def field_errors(lat, cfg, body, chi, f):
+    rho, ux, uy = lat.get_fields()
+    r0, x0, y0 = o.fields(cfg, body, chi, f)
+    return rel_linf(rho - 1, r0 - 1), rel_linf(ux, x0), rel_linf(uy, y0)
+
+
+_NACA512 = {}
+
+
+def naca512_oracle():
+    """FP64 oracle of NACA 0012 at 10 degrees on 512 x 256, 1000 steps (cached)."""
+    if not _NACA512:
+        w = W.naca(10.0, dtype="f64", nx=512, ny=256, steps=1000)
+        cfg, body, chi, f, pts = oracle_setup(w)
+        mh, sh, _, _ = o.run(cfg, body, f, chi, w.steps, sim_pts=pts)
+        _NACA512.update(cfg=cfg, body=body, chi=chi, f=f, mh=mh, sh=sh)
+    return _NACA512
+
+
+def test_fp32_fields_after_1000_steps():
+    """NACA 0012 at 10 degrees on 512 x 256 (C = 50), FP32: 1000 steps, field
+    error <= 1e-5 relative for rho - 1, u_x, u_y; forces within 1e-3."""
+    w = W.naca(10.0, dtype="f32", nx=512, ny=256, steps=1000)
+    lat = lattice(w)
+    lat.step(w.steps)
+    r = naca512_oracle()
+    mh, sh = r["mh"], r["sh"]
+    errs = field_errors(lat, r["cfg"], r["body"], r["chi"], r["f"])
+    print("f32", errs)
+    assert max(errs) <= 1e-5, errs
+    fm, fs = lat.force_mem(), lat.force_sim()
+    for g, r in ((fm, mh[-1]), (fs, sh[-1])):
+        assert abs(g[0] - r[0]) <= 1e-3 * abs(r[0])
+        assert abs(g[1] - r[1]) <= 1e-3 * abs(r[1])
+
+
+@pytest.mark.parametrize("dtype,tol", [("f16", 3e-2), ("bf16", 2e-1)])
+def test_16bit_storage_error_is_bounded(dtype, tol):
+    """Offsets f - w stored in FP16 / BF16 (FP32 collide): field errors after
+    1000 steps stay within the storage precision times a modest growth."""
+    w = W.naca(10.0, dtype=dtype, nx=512, ny=256, steps=1000)
+    lat = lattice(w)
+    lat.step(w.steps)
+    r = naca512_oracle()
+    errs = field_errors(lat, r["cfg"], r["body"], r["chi"], r["f"])
+    print(dtype, errs)
+    assert max(errs) <= tol, errs
+
+
+# ---------------------------------------------------------------------------
+# full-size configuration (2048 x 1024 FP32), sampled against the oracle
+# ---------------------------------------------------------------------------
+def test_naca_full_size_sampled():
+    """The 2048 x 1024 NACA 0012 lattice in the launch configuration the
+    benchmark times (CUDA graph of steps): after 40 steps, 2000 sampled nodes
+    and both forces agree with the FP64 oracle run at full size."""
+    w = W.naca(15.0, dtype="f32", steps=40)
+    lat = lattice(w)
+    lat.step(w.steps)
+    cfg, body, chi, f, pts = oracle_setup(w)
+    mh, sh, _, _ = o.run(cfg, body, f, chi, w.steps, sim_pts=pts)
+    rng = np.random.default_rng(5)
+    idx = rng.integers(0, w.nx * w.ny, 2000)
+    rho, ux, uy = lat.get_fields()
+    r0, x0, y0 = o.fields(cfg, body, chi, f)
+    for g, r, sub in ((rho, r0, 1.0), (ux, x0, 0.0), (uy, y0, 0.0)):
+        g, r = g.ravel()[idx] - sub, r.ravel()[idx] - sub
+        assert np.abs(g - r).max() <= 1e-5 * np.abs(r).max()
+    for g, r in ((lat.force_mem(), mh[-1]), (lat.force_sim(), sh[-1])):
+        assert np.abs(g[:2] - r[:2]).max() <= 1e-3 * np.abs(r[:2]).max()
+
+
+def test_graph_replay_equals_single_launches():
+    w = W.naca(5.0, dtype="f32", nx=256, ny=128)
+    a, b = lattice(w), lattice(w)
+    a.step(97)  # 1 + 32 * 3 with graphs
+    for _ in range(97):
+        b.step(1)
+    assert np.array_equal(a.get_f(), b.get_f())
+    np.testing.assert_array_equal(a.history(V.MEM, 97), b.history(V.MEM, 97))
+    assert a.launches >= 97
+
+
+# ---------------------------------------------------------------------------
+# error behaviour
+# ---------------------------------------------------------------------------
+def test_error_statuses():
+    import torch
+    w = W.naca(0.0, nx=256, ny=128)
+    cfg = V.config_of(w)
+    lat = V.Lattice(cfg)
+    with pytest.raises(V.VplbmError) as e:
+        lat.step(1)
+    assert e.value.status == V.ESTATE
+    lat.set_body(V.body_of(w))
+    with pytest.raises(V.VplbmError) as e:
+        lat.force_mem()
+    assert e.value.status == V.ESTATE
+    lat.step(0)
+    assert lat.steps == 0
+    with pytest.raises(V.VplbmError) as e:
+        V.vplbm_step(lat.ctx, -1)
+    assert e.value.status == V.EINVAL
+    far = V.body_of(w)
+    far.x_c = 250.0
+    with pytest.raises(V.VplbmError) as e:
+        lat.set_body(far)
+    assert e.value.status == V.EINVAL
+    # workspace too small / misaligned
+    n = V.vplbm_workspace_bytes(cfg)
+    ws = torch.empty(n + 512, dtype=torch.uint8, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    with pytest.raises(V.VplbmError) as e:
+        V.vplbm_create(cfg, base, n - 1, 0)
+    assert e.value.status == V.ENOMEM
+    with pytest.raises(V.VplbmError) as e:
+        V.vplbm_create(cfg, base + 8, n, 0)
+    assert e.value.status == V.EINVAL
+
+
+def test_instability_is_latched():
+    """tau+ near 1/2 with a fast inflow blows up; the guard latches EUNSTABLE
+    and the context stays usable."""
+    w = W.Workload(name="unstable", nx=64, ny=32, dtype="f32", collision="bgk", tau_plus=0.5001,
+                   u_in=(0.45, 0.0), bc=("inlet", "outlet", "periodic", "periodic"),
+                   body=W.Body("disk", length=10.0, x_c=20.0, y_c=16.0), steps=2000)
+    lat = lattice(w)
+    lat.step(w.steps)
+    with pytest.raises(V.VplbmError) as e:
+        lat.check()
+    assert e.value.status == V.EUNSTABLE
+    lat.set_body(V.body_of(w.with_(u_in=(0.01, 0.0))))
