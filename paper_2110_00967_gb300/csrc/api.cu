@@ -31,13 +31,22 @@ size_t elem_bytes(int dtype) {
 }
 
 struct Layout {
-  size_t buf[2], prev[2], chi, partials, sim_pts, sim_contrib, sim_nodes, hist, body, sums,
-      counts, dev_step, ticket, status, total;
+  size_t buf[2], prev[2], chi, partials, sim_pts, sim_contrib, sim_nodes, hist, body[2],
+      region[2], sums, counts, dev_step, ticket, status, total;
 };
 
 int effective_max_sim(const vplbm_config &c) { return c.max_sim_points > 0 ? c.max_sim_points : 4096; }
 int effective_hist(const vplbm_config &c) { return c.history_len > 0 ? c.history_len : 1024; }
 int pitch_of(int nx) { return (int)align_up((size_t)nx, 64); }
+
+// elements between two population planes: the padded rows plus an offset
+// that keeps the nine planes from sharing address bits with each other
+#ifndef VPLBM_PLANE_PAD
+#define VPLBM_PLANE_PAD 0
+#endif
+int64_t plane_of(const vplbm_config &c) {
+  return (int64_t)pitch_of(c.nx) * c.ny + VPLBM_PLANE_PAD;
+}
 
 Layout make_layout(const vplbm_config &c) {
   Layout l{};
@@ -47,20 +56,23 @@ Layout make_layout(const vplbm_config &c) {
     off = align_up(off + bytes, kAlign);
     return at;
   };
-  const size_t plane = (size_t)pitch_of(c.nx) * (size_t)c.ny;
+  const size_t plane = (size_t)plane_of(c);
   const size_t fbytes = 9 * plane * elem_bytes(c.dtype);
   l.buf[0] = take(fbytes);
   l.buf[1] = take(fbytes);
   l.prev[0] = take(3 * (size_t)c.ny * sizeof(double));
   l.prev[1] = take(3 * (size_t)c.ny * sizeof(double));
-  l.chi = take(plane);
-  l.partials = take((size_t)kMaxBlocks * 3 * sizeof(double));
+  l.chi = take((size_t)pitch_of(c.nx) * (size_t)c.ny);
+  l.partials = take((size_t)kRegionCapacity * 3 * sizeof(double));
   const size_t ms = (size_t)effective_max_sim(c);
   l.sim_pts = take(ms * sizeof(SimPoint));
   l.sim_contrib = take(ms * 3 * sizeof(double));
   l.sim_nodes = take(ms * sizeof(int32_t));
   l.hist = take((size_t)effective_hist(c) * 6 * sizeof(double));
-  l.body = take(sizeof(BodyState));
+  l.body[0] = take(sizeof(BodyState));
+  l.body[1] = take(sizeof(BodyState));
+  l.region[0] = take(sizeof(ForceRegion));
+  l.region[1] = take(sizeof(ForceRegion));
   l.sums = take(6 * sizeof(double));
   l.counts = take(2 * sizeof(long long));
   l.dev_step = take(sizeof(long long));
@@ -187,14 +199,15 @@ struct vplbm_ctx {
   int device;
   char *ws;
   void *buf[2];
-  double *prev[2];
+  void *prev[2];  // outlet column in the compute type
   uint8_t *chi;
   double *partials;
   SimPoint *sim_pts;
   double *sim_contrib;
   int32_t *sim_nodes;
   double *hist;
-  BodyState *body;
+  BodyState *body[2];
+  ForceRegion *region[2];
   double *sums;
   long long *counts;
   long long *dev_step;
@@ -205,10 +218,10 @@ struct vplbm_ctx {
   bool has_body = false;
   vplbm_body body_cfg{};
   BodyState body_host{};
+  ForceRegion region_host{};
   int n_sim = 0;
   int sim_every = 0;  // effective
   long long steps = 0;
-  int grid = 1;
   int64_t launches = 0;
   cudaGraphExec_t graph = nullptr;  // 2 * kGraphPairs steps starting from buffer 0
   std::string err;
@@ -243,13 +256,16 @@ StepArgs step_args(vplbm_ctx *c, int src, bool do_sim) {
   a.prev_src = c->prev[src];
   a.prev_dst = c->prev[1 - src];
   a.chi = c->chi;
-  a.body = c->body;
+  a.body_src = c->body[src];
+  a.body_dst = c->body[1 - src];
+  a.reg_src = c->region[src];
+  a.reg_dst = c->region[1 - src];
   a.mem_partials = c->partials;
   a.sim_pts = c->sim_pts;
   a.sim_contrib = c->sim_contrib;
   a.sim_nodes = c->sim_nodes;
   a.n_sim = c->n_sim;
-  a.do_sim = do_sim ? 1 : 0;
+  a.sim_blocks = do_sim ? (c->n_sim + kThreads - 1) / kThreads : 0;
   a.hist = c->hist;
   a.hist_len = effective_hist(c->cfg);
   a.sums = c->sums;
@@ -264,7 +280,8 @@ StepArgs step_args(vplbm_ctx *c, int src, bool do_sim) {
   a.half_pen = c->half_pen;
   a.tau_plus = c->cfg.tau_plus;
   a.ntiles_x = (c->L.nx + kTileX - 1) / kTileX;
-  a.ntiles = a.ntiles_x * ((c->L.ny + kTileY - 1) / kTileY);
+  a.ntiles_y = (c->L.ny + kTileY - 1) / kTileY;
+  a.region_capacity = kRegionCapacity;
   return a;
 }
 
@@ -274,7 +291,7 @@ bool sim_due(const vplbm_ctx *c, long long step) {
 
 vplbm_status one_step(vplbm_ctx *c, cudaStream_t s) {
   const StepArgs a = step_args(c, c->cur, sim_due(c, c->steps));
-  VPLBM_CUDA(c, launch_step(c->cfg.dtype, !c->pre, a, c->grid, s));
+  VPLBM_CUDA(c, launch_step(c->cfg.dtype, !c->pre, a, s));
   ++c->launches;
   c->cur = 1 - c->cur;
   c->pre = false;
@@ -293,7 +310,7 @@ vplbm_status ensure_graph(vplbm_ctx *c) {
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k) {
     const StepArgs a = step_args(c, k & 1, c->sim_every == 1 && c->n_sim > 0);
-    e = launch_step(c->cfg.dtype, true, a, c->grid, c->capture_stream);
+    e = launch_step(c->cfg.dtype, true, a, c->capture_stream);
   }
   cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
   if (e != cudaSuccess) {
@@ -354,15 +371,18 @@ vplbm_status vplbm_create(const vplbm_config *cfg, void *dev_workspace, size_t b
   c->ws = (char *)dev_workspace;
   c->buf[0] = c->ws + lay.buf[0];
   c->buf[1] = c->ws + lay.buf[1];
-  c->prev[0] = (double *)(c->ws + lay.prev[0]);
-  c->prev[1] = (double *)(c->ws + lay.prev[1]);
+  c->prev[0] = c->ws + lay.prev[0];
+  c->prev[1] = c->ws + lay.prev[1];
   c->chi = (uint8_t *)(c->ws + lay.chi);
   c->partials = (double *)(c->ws + lay.partials);
   c->sim_pts = (SimPoint *)(c->ws + lay.sim_pts);
   c->sim_contrib = (double *)(c->ws + lay.sim_contrib);
   c->sim_nodes = (int32_t *)(c->ws + lay.sim_nodes);
   c->hist = (double *)(c->ws + lay.hist);
-  c->body = (BodyState *)(c->ws + lay.body);
+  c->body[0] = (BodyState *)(c->ws + lay.body[0]);
+  c->body[1] = (BodyState *)(c->ws + lay.body[1]);
+  c->region[0] = (ForceRegion *)(c->ws + lay.region[0]);
+  c->region[1] = (ForceRegion *)(c->ws + lay.region[1]);
   c->sums = (double *)(c->ws + lay.sums);
   c->counts = (long long *)(c->ws + lay.counts);
   c->dev_step = (long long *)(c->ws + lay.dev_step);
@@ -373,16 +393,20 @@ vplbm_status vplbm_create(const vplbm_config *cfg, void *dev_workspace, size_t b
   L.nx = cfg->nx;
   L.ny = cfg->ny;
   L.pitch = pitch_of(cfg->nx);
-  L.plane = (int64_t)L.pitch * L.ny;
+  L.plane = plane_of(*cfg);
   for (int k = 0; k < 4; ++k) L.bc[k] = cfg->bc[k];
   for (int a = 0; a < 9; ++a) {
     // inlet bounce-back from a wall moving at u_in: 2 w_a rho_w (c_a.u_in) / cs2, rho_w = 1
     const double cu = cx_of(a) * cfg->u_in[0] + cy_of(a) * cfg->u_in[1];
     L.kin[a] = 2.0 * w_of(a) * cu * 3.0;
+    L.kin_f[a] = (float)L.kin[a];
   }
   L.uc = sqrt(cfg->u_in[0] * cfg->u_in[0] + cfg->u_in[1] * cfg->u_in[1]);
   L.bf[0] = cfg->body_force[0];
   L.bf[1] = cfg->body_force[1];
+  L.uc_f = (float)L.uc;
+  L.bf_f[0] = (float)L.bf[0];
+  L.bf_f[1] = (float)L.bf[1];
 
   const double tp = cfg->tau_plus;
   const double tm = cfg->collision == VPLBM_BGK ? tp : cfg->lambda_trt / (tp - 0.5) + 0.5;
@@ -393,11 +417,11 @@ vplbm_status vplbm_create(const vplbm_config *cfg, void *dev_workspace, size_t b
                                                                                   : c->a_plus;
   c->half_pen = 0.5 / cfg->eta;
 
-  int sms = 1;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const int per_sm = step_blocks_per_sm(cfg->dtype, true);
-  const int ntiles = ((L.nx + kTileX - 1) / kTileX) * ((L.ny + kTileY - 1) / kTileY);
-  c->grid = std::max(1, std::min({sms * per_sm, ntiles, kMaxBlocks}));
+  const int64_t ntiles = (int64_t)((L.nx + kTileX - 1) / kTileX) * ((L.ny + kTileY - 1) / kTileY);
+  if (ntiles + 64 > (int64_t)INT32_MAX) {
+    delete c;
+    return fail(nullptr, VPLBM_EINVAL, "lattice too large for one launch");
+  }
 
   cudaError_t e = cudaMemsetAsync(c->ws, 0, lay.total, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -437,6 +461,7 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
   bs.gy = b->gravity[1];
   bs.moving = b->moving;
   bs.estimator = b->estimator;
+  body_sync_f32(bs);
   std::vector<SimPoint> pts;
   int n_sim = 0;
   if (b->kind != VPLBM_BODY_NONE) {
@@ -469,6 +494,21 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
     if (!(x0 >= 0.0 && y0 >= 0.0 && x1 <= L.nx - 1.0 && y1 <= L.ny - 1.0))
       return fail(c, VPLBM_EINVAL, "body does not fit in the lattice");
   }
+  // force region: tiles around the body (its farthest polygon point from the
+  // reference point sets the extent); tile (0, 0) alone for an empty lattice
+  double extent = 0.0;
+  for (const SimPoint &p : pts)
+    extent = std::max(extent, sqrt(p.dx * p.dx + p.dy * p.dy) + 0.5 * p.s);
+  const int ntx = (L.nx + kTileX - 1) / kTileX, nty = (L.ny + kTileY - 1) / kTileY;
+  ForceRegion reg{};
+  if (b->kind != VPLBM_BODY_NONE) {
+    reg = make_region(L, b->x_c, b->y_c, extent, ntx, nty);
+    reg.error = 0;
+    if (reg.count > kRegionCapacity)
+      return fail(c, VPLBM_EINVAL, fmt("body too large: %d force-region tiles (capacity %d)", reg.count, kRegionCapacity));
+  } else {
+    reg.count = 1;
+  }
   c->body_cfg = *b;
   c->body_host = bs;
   c->n_sim = n_sim;
@@ -478,19 +518,23 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
     c->graph = nullptr;
   }
   cudaStream_t s = c->stream;
-  VPLBM_CUDA(c, cudaMemcpyAsync(c->body, &c->body_host, sizeof(BodyState), cudaMemcpyHostToDevice, s));
+  c->region_host = reg;
+  for (int k = 0; k < 2; ++k) {
+    VPLBM_CUDA(c, cudaMemcpyAsync(c->body[k], &c->body_host, sizeof(BodyState), cudaMemcpyHostToDevice, s));
+    VPLBM_CUDA(c, cudaMemcpyAsync(c->region[k], &c->region_host, sizeof(ForceRegion), cudaMemcpyHostToDevice, s));
+  }
   if (n_sim > 0)
     VPLBM_CUDA(c, cudaMemcpyAsync(c->sim_pts, pts.data(), n_sim * sizeof(SimPoint), cudaMemcpyHostToDevice, s));
-  VPLBM_CUDA(c, cudaMemsetAsync(c->chi, 0, (size_t)L.plane, s));
+  VPLBM_CUDA(c, cudaMemsetAsync(c->chi, 0, (size_t)L.pitch * L.ny, s));
   if (b->kind != VPLBM_BODY_NONE) {
-    VPLBM_CUDA(c, launch_raster(L, c->body, c->chi, 0, 0, L.nx - 1, L.ny - 1, s));
+    VPLBM_CUDA(c, launch_raster(L, c->body[0], c->chi, 0, 0, L.nx - 1, L.ny - 1, s));
     VPLBM_CUDA(c, launch_interface(L, c->chi, 0, 0, L.nx - 1, L.ny - 1, s));
     c->launches += 2;
   }
-  VPLBM_CUDA(c, launch_init(c->cfg.dtype, L, c->body, c->chi, c->buf[0], c->cfg.u_in[0], c->cfg.u_in[1], s));
+  VPLBM_CUDA(c, launch_init(c->cfg.dtype, L, c->body[0], c->chi, c->buf[0], c->cfg.u_in[0], c->cfg.u_in[1], s));
   ++c->launches;
   // histories, sums, counters, status
-  VPLBM_CUDA(c, cudaMemsetAsync(c->ws + c->lay.hist, 0, c->lay.body - c->lay.hist, s));
+  VPLBM_CUDA(c, cudaMemsetAsync(c->ws + c->lay.hist, 0, c->lay.body[0] - c->lay.hist, s));
   VPLBM_CUDA(c, cudaMemsetAsync(c->ws + c->lay.sums, 0, c->lay.total - c->lay.sums, s));
   VPLBM_CUDA(c, cudaMemsetAsync(c->prev[0], 0, 3 * (size_t)L.ny * sizeof(double), s));
   VPLBM_CUDA(c, cudaMemsetAsync(c->prev[1], 0, 3 * (size_t)L.ny * sizeof(double), s));
@@ -630,7 +674,7 @@ vplbm_status vplbm_get_fields(vplbm_ctx *c, double *rho, double *ux, double *uy)
   if (!rho || !ux || !uy) return fail(c, VPLBM_EINVAL, "NULL output");
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "no state yet");
   VPLBM_CUDA(c, launch_get_fields(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], c->chi,
-                                  c->body, c->half_pen, rho, ux, uy, c->stream));
+                                  c->body[c->cur], c->half_pen, rho, ux, uy, c->stream));
   ++c->launches;
   return VPLBM_OK;
 }
@@ -645,7 +689,7 @@ vplbm_status vplbm_set_state(vplbm_ctx *c, const double *f_dev, const double *pr
   VPLBM_CUDA(c, launch_set_state(c->cfg.dtype, c->L, f_dev, c->buf[c->cur], c->stream));
   ++c->launches;
   if (post_collision && prev_dev) {
-    VPLBM_CUDA(c, launch_set_prev(c->L, prev_dev, c->prev[c->cur], c->stream));
+    VPLBM_CUDA(c, launch_set_prev(c->cfg.dtype, c->L, prev_dev, c->prev[c->cur], c->stream));
     ++c->launches;
   }
   c->pre = post_collision == 0;
@@ -664,7 +708,7 @@ vplbm_status vplbm_get_body(vplbm_ctx *c, double state[6]) {
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!state) return fail(c, VPLBM_EINVAL, "NULL output");
   BodyState b;
-  VPLBM_CUDA(c, cudaMemcpyAsync(&b, c->body, sizeof b, cudaMemcpyDeviceToHost, c->stream));
+  VPLBM_CUDA(c, cudaMemcpyAsync(&b, c->body[c->cur], sizeof b, cudaMemcpyDeviceToHost, c->stream));
   if (vplbm_status st = sync(c)) return st;
   state[0] = b.xg;
   state[1] = b.yg;

@@ -61,7 +61,8 @@ __global__ void init_kernel(Lattice L, const BodyState *body, const uint8_t *chi
 }
 
 template <typename S, bool kGather>
-__global__ void get_f_kernel(Lattice L, const S *buf, const double *prev, double *out) {
+__global__ void get_f_kernel(Lattice L, const S *buf, const typename Store<S>::T *prev,
+                             double *out) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = (int64_t)L.nx * L.ny;
   if (k >= n) return;
@@ -73,7 +74,8 @@ __global__ void get_f_kernel(Lattice L, const S *buf, const double *prev, double
 
 // macroscopic fields of Eqs. updatestep and updatestepm, FP64
 template <typename S, bool kGather>
-__global__ void get_fields_kernel(Lattice L, const S *buf, const double *prev, const uint8_t *chi,
+__global__ void get_fields_kernel(Lattice L, const S *buf, const typename Store<S>::T *prev,
+                                  const uint8_t *chi,
                                   const BodyState *body, double half_pen, double *rho_o,
                                   double *ux_o, double *uy_o) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -115,15 +117,17 @@ __global__ void set_state_kernel(Lattice L, const double *f, S *buf) {
     buf[(int64_t)a * L.plane + node] = Store<S>::from_double(f[a * n + k] - w_of(a));
 }
 
-// outlet column (a = 3, 6, 7 at i = nx - 1) of a pre-collision FP64 field
-__global__ void set_prev_kernel(Lattice L, const double *f, double *prev) {
+// outlet column (a = 3, 6, 7 at i = nx - 1) of a pre-collision FP64 field,
+// kept as offsets in the compute type
+template <typename T>
+__global__ void set_prev_kernel(Lattice L, const double *f, T *prev) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= L.ny) return;
   const int64_t n = (int64_t)L.nx * L.ny;
   const int64_t k = (int64_t)j * L.nx + (L.nx - 1);
-  prev[0 * L.ny + j] = f[3 * n + k] - w_of(3);
-  prev[1 * L.ny + j] = f[6 * n + k] - w_of(6);
-  prev[2 * L.ny + j] = f[7 * n + k] - w_of(7);
+  prev[0 * L.ny + j] = (T)(f[3 * n + k] - w_of(3));
+  prev[1 * L.ny + j] = (T)(f[6 * n + k] - w_of(6));
+  prev[2 * L.ny + j] = (T)(f[7 * n + k] - w_of(7));
 }
 
 __global__ void get_mask_kernel(Lattice L, const uint8_t *chi, uint8_t *out) {
@@ -134,8 +138,10 @@ __global__ void get_mask_kernel(Lattice L, const uint8_t *chi, uint8_t *out) {
 }
 
 template <typename S>
-cudaError_t get_f_t(bool gather, const Lattice &L, const void *buf, const double *prev,
+cudaError_t get_f_t(bool gather, const Lattice &L, const void *buf, const void *prev_v,
                     double *out, cudaStream_t s) {
+  using T = typename Store<S>::T;
+  const T *prev = static_cast<const T *>(prev_v);
   const int g = blocks_for((int64_t)L.nx * L.ny);
   if (gather)
     get_f_kernel<S, true><<<g, kAuxThreads, 0, s>>>(L, (const S *)buf, prev, out);
@@ -145,9 +151,11 @@ cudaError_t get_f_t(bool gather, const Lattice &L, const void *buf, const double
 }
 
 template <typename S>
-cudaError_t get_fields_t(bool gather, const Lattice &L, const void *buf, const double *prev,
+cudaError_t get_fields_t(bool gather, const Lattice &L, const void *buf, const void *prev_v,
                          const uint8_t *chi, const BodyState *body, double half_pen, double *rho,
                          double *ux, double *uy, cudaStream_t s) {
+  using T = typename Store<S>::T;
+  const T *prev = static_cast<const T *>(prev_v);
   const int g = blocks_for((int64_t)L.nx * L.ny);
   if (gather)
     get_fields_kernel<S, true>
@@ -192,7 +200,7 @@ cudaError_t launch_init(int dtype, const Lattice &L, const BodyState *body, cons
 }
 
 cudaError_t launch_get_f(int dtype, bool gather, const Lattice &L, const void *buf,
-                         const double *prev, double *out, cudaStream_t s) {
+                         const void *prev, double *out, cudaStream_t s) {
   switch (dtype) {
     case VPLBM_F64: return get_f_t<double>(gather, L, buf, prev, out, s);
     case VPLBM_F32: return get_f_t<float>(gather, L, buf, prev, out, s);
@@ -203,7 +211,7 @@ cudaError_t launch_get_f(int dtype, bool gather, const Lattice &L, const void *b
 }
 
 cudaError_t launch_get_fields(int dtype, bool gather, const Lattice &L, const void *buf,
-                              const double *prev, const uint8_t *chi, const BodyState *body,
+                              const void *prev, const uint8_t *chi, const BodyState *body,
                               double half_pen, double *rho, double *ux, double *uy,
                               cudaStream_t s) {
   switch (dtype) {
@@ -231,8 +239,12 @@ cudaError_t launch_set_state(int dtype, const Lattice &L, const double *f, void 
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_prev(const Lattice &L, const double *f, double *prev, cudaStream_t s) {
-  set_prev_kernel<<<blocks_for(L.ny), kAuxThreads, 0, s>>>(L, f, prev);
+cudaError_t launch_set_prev(int dtype, const Lattice &L, const double *f, void *prev,
+                            cudaStream_t s) {
+  if (dtype == VPLBM_F64)
+    set_prev_kernel<double><<<blocks_for(L.ny), kAuxThreads, 0, s>>>(L, f, (double *)prev);
+  else
+    set_prev_kernel<float><<<blocks_for(L.ny), kAuxThreads, 0, s>>>(L, f, (float *)prev);
   return cudaGetLastError();
 }
 

@@ -37,10 +37,18 @@ __host__ __device__ __forceinline__ constexpr double w_of(int a) {
   return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
-constexpr int kTileX = 128;  // threads along x per block (4 warps per row)
-constexpr int kTileY = 2;    // rows per block
+// lattice tile of one block, one node per thread
+#ifndef VPLBM_TILE_X
+#define VPLBM_TILE_X 128
+#endif
+#ifndef VPLBM_TILE_Y
+#define VPLBM_TILE_Y 2
+#endif
+constexpr int kTileX = VPLBM_TILE_X;  // threads along x (whole warps per row)
+constexpr int kTileY = VPLBM_TILE_Y;  // rows
 constexpr int kThreads = kTileX * kTileY;
-constexpr int kMaxBlocks = 8192;  // capacity of the MEM partial array
+constexpr int kRegionCapacity = 16384;  // force-region tiles (MEM partials)
+constexpr int kSimThreads = 128;        // threads per SIM block
 
 // mask byte bits
 constexpr uint8_t kSolid = 1;      // chi = 1
@@ -59,6 +67,7 @@ template <>
 struct Store<double> {
   using T = double;
   static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+  static __device__ __forceinline__ double ld_own(const double *p) { return __ldcg(p); }
   static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
   static __device__ __forceinline__ double from_double(double v) { return v; }
 };
@@ -66,6 +75,7 @@ template <>
 struct Store<float> {
   using T = float;
   static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+  static __device__ __forceinline__ float ld_own(const float *p) { return __ldcg(p); }
   static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
   static __device__ __forceinline__ float from_double(double v) { return __double2float_rn(v); }
 };
@@ -73,6 +83,7 @@ template <>
 struct Store<__half> {
   using T = float;
   static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ float ld_own(const __half *p) { return __half2float(__ldcg(p)); }
   static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
   static __device__ __forceinline__ __half from_double(double v) { return __double2half(v); }
 };
@@ -81,6 +92,9 @@ struct Store<__nv_bfloat16> {
   using T = float;
   static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) {
     return __bfloat162float(__ldg(p));
+  }
+  static __device__ __forceinline__ float ld_own(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldcg(p));
   }
   static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) {
     *p = __float2bfloat16_rn(v);
@@ -106,7 +120,33 @@ struct BodyState {
   int32_t moving;
   int32_t estimator;
   int32_t pad;
+  float f_ux, f_uy, f_omega, f_xg, f_yg, f_pad;  // FP32 copies for FP32 paths
 };
+
+// keeps the FP32 copies in step with the FP64 state
+__host__ __device__ inline void body_sync_f32(BodyState &b) {
+  b.f_ux = (float)b.ux;
+  b.f_uy = (float)b.uy;
+  b.f_omega = (float)b.omega;
+  b.f_xg = (float)b.xg;
+  b.f_yg = (float)b.yg;
+}
+
+// rigid velocity u_s = U + Omega x (x - x_G) at node (i, j), in the compute type
+template <typename T>
+__device__ __forceinline__ void solid_velocity(const BodyState &b, int i, int j, T &usx, T &usy);
+template <>
+__device__ __forceinline__ void solid_velocity<double>(const BodyState &b, int i, int j,
+                                                       double &usx, double &usy) {
+  usx = b.ux - b.omega * ((double)j - b.yg);
+  usy = b.uy + b.omega * ((double)i - b.xg);
+}
+template <>
+__device__ __forceinline__ void solid_velocity<float>(const BodyState &b, int i, int j,
+                                                      float &usx, float &usy) {
+  usx = b.f_ux - b.f_omega * ((float)j - b.f_yg);
+  usy = b.f_uy + b.f_omega * ((float)i - b.f_xg);
+}
 
 struct SimPoint {
   double dx, dy;  // offset of the integration point from the reference point
@@ -126,7 +166,30 @@ struct Lattice {
   double kin[9];     // inlet bounce-back terms 2 w_a (c_a.u_in)/cs2
   double uc;         // convective outlet velocity |u_in|
   double bf[2];      // uniform body force density
+  float kin_f[9];    // the same in FP32 (no FP64 work on FP32 paths)
+  float uc_f;
+  float bf_f[2];
 };
+
+// lattice constants in the compute type
+template <typename T>
+__device__ __forceinline__ T lat_kin(const Lattice &L, int a);
+template <>
+__device__ __forceinline__ double lat_kin<double>(const Lattice &L, int a) { return L.kin[a]; }
+template <>
+__device__ __forceinline__ float lat_kin<float>(const Lattice &L, int a) { return L.kin_f[a]; }
+template <typename T>
+__device__ __forceinline__ T lat_uc(const Lattice &L);
+template <>
+__device__ __forceinline__ double lat_uc<double>(const Lattice &L) { return L.uc; }
+template <>
+__device__ __forceinline__ float lat_uc<float>(const Lattice &L) { return L.uc_f; }
+template <typename T>
+__device__ __forceinline__ T lat_bf(const Lattice &L, int k);
+template <>
+__device__ __forceinline__ double lat_bf<double>(const Lattice &L, int k) { return L.bf[k]; }
+template <>
+__device__ __forceinline__ float lat_bf<float>(const Lattice &L, int k) { return L.bf_f[k]; }
 
 // Pull-form streaming: the pre-collision population a at node (i, j) of the
 // time level whose post-collision field is `post` (previous level) and whose
@@ -154,7 +217,7 @@ __device__ __forceinline__ typename Store<S>::T gather_core(const S *post, const
   if (xin && yin) return pop_at(post, L, a, si, sj);
   if (!xin) {
     const int kind = L.bc[si < 0 ? 0 : 1];
-    if (kind == VPLBM_INLET_BB) return pop_at(post, L, opp_of(a), i, j) + (T)L.kin[a];
+    if (kind == VPLBM_INLET_BB) return pop_at(post, L, opp_of(a), i, j) + lat_kin<T>(L, a);
     return pop_at(post, L, opp_of(a), i, j);  // no-slip bounce-back
   }
   const int kind = L.bc[sj < 0 ? 2 : 3];
@@ -164,15 +227,19 @@ __device__ __forceinline__ typename Store<S>::T gather_core(const S *post, const
 
 __device__ __forceinline__ int outlet_slot(int a) { return a == 3 ? 0 : (a == 6 ? 1 : 2); }
 
+// The outlet column is kept in the compute type T (FP64 for the FP64 form,
+// FP32 otherwise), [3][ny] for a = 3, 6, 7.
 template <typename S>
-__device__ __forceinline__ typename Store<S>::T gather(const S *post, const double *prev,
+__device__ __forceinline__ typename Store<S>::T gather(const S *post,
+                                                        const typename Store<S>::T *prev,
                                                         const Lattice &L, int a, int i, int j) {
   using T = typename Store<S>::T;
   if (cx_of(a) < 0 && i == L.nx - 1 && L.bc[1] == VPLBM_OUTLET_CONVECTIVE) {
     // convective outlet: f^{n+1}(N-1) = (f^n(N-1) + U_c f^{n+1}(N-2)) / (1 + U_c)
     const T inner = gather_core(post, L, a, i - 1, j);
-    const T old = (T)prev[outlet_slot(a) * L.ny + j];
-    return (old + (T)L.uc * inner) / ((T)1 + (T)L.uc);
+    const T old = prev[outlet_slot(a) * L.ny + j];
+    const T uc = lat_uc<T>(L);
+    return (old + uc * inner) / ((T)1 + uc);
   }
   return gather_core(post, L, a, i, j);
 }
@@ -180,7 +247,8 @@ __device__ __forceinline__ typename Store<S>::T gather(const S *post, const doub
 // Pre-collision population of the current level: gathered from the previous
 // post-collision field, or read in place when the state is pre-collision.
 template <typename S, bool kGather>
-__device__ __forceinline__ typename Store<S>::T pre_pop(const S *buf, const double *prev,
+__device__ __forceinline__ typename Store<S>::T pre_pop(const S *buf,
+                                                         const typename Store<S>::T *prev,
                                                          const Lattice &L, int a, int i, int j) {
   if (kGather) return gather(buf, prev, L, a, i, j);
   return pop_at(buf, L, a, i, j);
@@ -237,6 +305,20 @@ __device__ __forceinline__ bool neighbour(const Lattice &L, int a, int i, int j,
 }
 
 // ---------------------------------------------------------------------------
+// the force region: the tiles that can hold MEM links (the body's box with a
+// margin); only their blocks and the SIM blocks take part in the reduction
+// ---------------------------------------------------------------------------
+struct ForceRegion {
+  int32_t ti0, ti1, tj0, tj1;  // inclusive tile ranges
+  int32_t count;               // number of region tiles (>= 1)
+  int32_t error;               // nonzero: the body left the lattice
+};
+
+// nodes of margin around a body for its force region; a moving body travels
+// less than one node per step, so its mask update stays inside the region
+constexpr int kRegionMargin = 4;
+
+// ---------------------------------------------------------------------------
 // parameters of the fused step kernel
 // ---------------------------------------------------------------------------
 struct StepArgs {
@@ -244,16 +326,19 @@ struct StepArgs {
   const void *src;      // populations: post-collision of level n-1 (gather)
                         // or pre-collision of level n (first step)
   void *dst;            // post-collision populations of level n
-  const double *prev_src;  // outlet column, pre-collision, level n-1
-  double *prev_dst;        // outlet column, pre-collision, level n
+  const void *prev_src;  // outlet column (compute type), pre-collision, level n-1
+  void *prev_dst;        // outlet column, pre-collision, level n
   uint8_t *chi;
-  BodyState *body;
-  double *mem_partials;  // [gridDim.x][3]
+  const BodyState *body_src;   // body at level n
+  BodyState *body_dst;         // body at level n + 1 (written by the tail)
+  const ForceRegion *reg_src;
+  ForceRegion *reg_dst;
+  double *mem_partials;  // [region tiles][3]
   const SimPoint *sim_pts;
   double *sim_contrib;   // [n_sim][3]
   int32_t *sim_nodes;    // [n_sim]
   int32_t n_sim;
-  int32_t do_sim;
+  int32_t sim_blocks;    // leading blocks that evaluate SIM (0: SIM not due)
   double *hist;          // [hist_len][6]
   int32_t hist_len;
   int32_t pad0;
@@ -267,12 +352,38 @@ struct StepArgs {
   double a_plus, a_minus;  // forcing prefactors
   double half_pen;         // dt/(2 eta)
   double tau_plus;
-  int32_t ntiles_x, ntiles;
+  int32_t ntiles_x, ntiles_y;
+  int32_t region_capacity;  // capacity of mem_partials in tiles
+  int32_t pad1;
 };
 
+// tile range of the force region of a body at (xg, yg) with radius-like extent r
+__host__ __device__ inline ForceRegion make_region(const Lattice &L, double xg, double yg,
+                                                   double r, int ntiles_x, int ntiles_y) {
+  ForceRegion g{};
+  const double m = r + kRegionMargin;
+  int i0 = (int)floor(xg - m), i1 = (int)ceil(xg + m);
+  int j0 = (int)floor(yg - m), j1 = (int)ceil(yg + m);
+  g.error = (i0 < -kRegionMargin || j0 < -kRegionMargin || i1 > L.nx - 1 + kRegionMargin ||
+             j1 > L.ny - 1 + kRegionMargin || !(xg == xg) || !(yg == yg))
+                ? 1
+                : 0;
+  i0 = i0 < 0 ? 0 : (i0 > L.nx - 1 ? L.nx - 1 : i0);
+  i1 = i1 < 0 ? 0 : (i1 > L.nx - 1 ? L.nx - 1 : i1);
+  j0 = j0 < 0 ? 0 : (j0 > L.ny - 1 ? L.ny - 1 : j0);
+  j1 = j1 < 0 ? 0 : (j1 > L.ny - 1 ? L.ny - 1 : j1);
+  g.ti0 = i0 / kTileX;
+  g.ti1 = i1 / kTileX;
+  g.tj0 = j0 / kTileY;
+  g.tj1 = j1 / kTileY;
+  if (g.ti1 > ntiles_x - 1) g.ti1 = ntiles_x - 1;
+  if (g.tj1 > ntiles_y - 1) g.tj1 = ntiles_y - 1;
+  g.count = (g.ti1 - g.ti0 + 1) * (g.tj1 - g.tj0 + 1);
+  return g;
+}
+
 // launches (step.cu)
-cudaError_t launch_step(int dtype, bool gather, const StepArgs &a, int grid, cudaStream_t s);
-int step_blocks_per_sm(int dtype, bool gather);
+cudaError_t launch_step(int dtype, bool gather, const StepArgs &a, cudaStream_t s);
 
 // auxiliary kernels (aux.cu)
 cudaError_t launch_raster(const Lattice &L, const BodyState *body, uint8_t *chi, int i0, int j0,
@@ -282,14 +393,15 @@ cudaError_t launch_interface(const Lattice &L, uint8_t *chi, int i0, int j0, int
 cudaError_t launch_init(int dtype, const Lattice &L, const BodyState *body, const uint8_t *chi,
                         void *buf, double u0x, double u0y, cudaStream_t s);
 cudaError_t launch_get_f(int dtype, bool gather, const Lattice &L, const void *buf,
-                         const double *prev, double *out, cudaStream_t s);
+                         const void *prev, double *out, cudaStream_t s);
 cudaError_t launch_get_fields(int dtype, bool gather, const Lattice &L, const void *buf,
-                              const double *prev, const uint8_t *chi, const BodyState *body,
+                              const void *prev, const uint8_t *chi, const BodyState *body,
                               double half_pen, double *rho, double *ux, double *uy,
                               cudaStream_t s);
 cudaError_t launch_set_state(int dtype, const Lattice &L, const double *f, void *buf,
                              cudaStream_t s);
-cudaError_t launch_set_prev(const Lattice &L, const double *f, double *prev, cudaStream_t s);
+cudaError_t launch_set_prev(int dtype, const Lattice &L, const double *f, void *prev,
+                            cudaStream_t s);
 cudaError_t launch_get_mask(const Lattice &L, const uint8_t *chi, uint8_t *out, cudaStream_t s);
 
 }  // namespace vplbm
