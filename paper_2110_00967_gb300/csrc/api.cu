@@ -31,8 +31,8 @@ size_t elem_bytes(int dtype) {
 }
 
 struct Layout {
-  size_t buf[2], prev[2], chi, partials, sim_pts, sim_contrib, sim_nodes, hist, body[2],
-      region[2], sums, counts, dev_step, ticket, status, total;
+  size_t buf[2], prev[2], chi, sim_pts, sim_nodes, hist, body[2], region[2], sums, counts,
+      dev_step, ticket, status, acc, total;
 };
 
 int effective_max_sim(const vplbm_config &c) { return c.max_sim_points > 0 ? c.max_sim_points : 4096; }
@@ -63,10 +63,8 @@ Layout make_layout(const vplbm_config &c) {
   l.prev[0] = take(3 * (size_t)c.ny * sizeof(double));
   l.prev[1] = take(3 * (size_t)c.ny * sizeof(double));
   l.chi = take((size_t)pitch_of(c.nx) * (size_t)c.ny);
-  l.partials = take((size_t)kRegionCapacity * 3 * sizeof(double));
   const size_t ms = (size_t)effective_max_sim(c);
   l.sim_pts = take(ms * sizeof(SimPoint));
-  l.sim_contrib = take(ms * 3 * sizeof(double));
   l.sim_nodes = take(ms * sizeof(int32_t));
   l.hist = take((size_t)effective_hist(c) * 6 * sizeof(double));
   l.body[0] = take(sizeof(BodyState));
@@ -78,6 +76,7 @@ Layout make_layout(const vplbm_config &c) {
   l.dev_step = take(sizeof(long long));
   l.ticket = take(sizeof(unsigned int));
   l.status = take(sizeof(int32_t));
+  l.acc = take(kAccWords * sizeof(unsigned long long));
   l.total = off;
   return l;
 }
@@ -177,7 +176,11 @@ bool build_polygon(const vplbm_body &b, int n, std::vector<SimPoint> &pts) {
       }
     }
     p.dir = best;
-    p.pad = 0;
+    p.f_dx = (float)p.dx;
+    p.f_dy = (float)p.dy;
+    p.f_nx = (float)p.nx;
+    p.f_ny = (float)p.ny;
+    p.f_s = (float)p.s;
   }
   return true;
 }
@@ -201,9 +204,8 @@ struct vplbm_ctx {
   void *buf[2];
   void *prev[2];  // outlet column in the compute type
   uint8_t *chi;
-  double *partials;
   SimPoint *sim_pts;
-  double *sim_contrib;
+  unsigned long long *acc;
   int32_t *sim_nodes;
   double *hist;
   BodyState *body[2];
@@ -224,6 +226,10 @@ struct vplbm_ctx {
   long long steps = 0;
   int64_t launches = 0;
   cudaGraphExec_t graph = nullptr;  // 2 * kGraphPairs steps starting from buffer 0
+  cudaStream_t side = nullptr;      // the special kernel's stream
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int region_slots = 1;             // blocks reserved for force-region tiles
+  double sim_const[3] = {0.0, 0.0, 0.0};  // -(1/3) sum S n and its moment
   std::string err;
   double s_plus, s_minus, a_plus, a_minus, half_pen;
 };
@@ -260,9 +266,9 @@ StepArgs step_args(vplbm_ctx *c, int src, bool do_sim) {
   a.body_dst = c->body[1 - src];
   a.reg_src = c->region[src];
   a.reg_dst = c->region[1 - src];
-  a.mem_partials = c->partials;
+  a.acc = c->acc;
   a.sim_pts = c->sim_pts;
-  a.sim_contrib = c->sim_contrib;
+  for (int k = 0; k < 3; ++k) a.sim_const[k] = c->sim_const[k];
   a.sim_nodes = c->sim_nodes;
   a.n_sim = c->n_sim;
   a.sim_blocks = do_sim ? (c->n_sim + kThreads - 1) / kThreads : 0;
@@ -279,8 +285,19 @@ StepArgs step_args(vplbm_ctx *c, int src, bool do_sim) {
   a.a_minus = c->a_minus;
   a.half_pen = c->half_pen;
   a.tau_plus = c->cfg.tau_plus;
+  a.f_s_plus = (float)a.s_plus;
+  a.f_s_minus = (float)a.s_minus;
+  a.f_a_plus = (float)a.a_plus;
+  a.f_a_minus = (float)a.a_minus;
+  a.f_half_pen = (float)a.half_pen;
+  a.f_sim_s = (float)(1.0 - 0.5 / a.tau_plus);
+  a.tile_w = kTileX;
   a.ntiles_x = (c->L.nx + kTileX - 1) / kTileX;
   a.ntiles_y = (c->L.ny + kTileY - 1) / kTileY;
+  a.all_tiles = 0;
+  a.n_edge = edge_count(c->L.nx, c->L.ny);
+  a.edge_blocks = (a.n_edge + kThreads - 1) / kThreads;
+  a.region_slots = c->region_slots;
   a.region_capacity = kRegionCapacity;
   return a;
 }
@@ -289,10 +306,31 @@ bool sim_due(const vplbm_ctx *c, long long step) {
   return c->sim_every > 0 && c->n_sim > 0 && step % c->sim_every == 0;
 }
 
+// One time step on stream s.  The first step after a pre-collision state
+// updates every tile with the special kernel.  Later steps split the nodes:
+// the special kernel (edge nodes, force region, SIM, tail: a few latency-bound
+// blocks) runs on the context's high-priority side stream beside the bulk
+// kernel (all other nodes, bandwidth-bound) on s; the two write disjoint
+// nodes, and s waits for both before the next step.
+cudaError_t queue_step(vplbm_ctx *c, cudaStream_t s, int src, bool pre, bool do_sim) {
+  StepArgs a = step_args(c, src, do_sim);
+  if (pre) {
+    a.all_tiles = 1;
+    ++c->launches;
+    return launch_special(c->cfg.dtype, false, a, s);
+  }
+  cudaError_t e = cudaEventRecord(c->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  if (e == cudaSuccess) e = launch_special(c->cfg.dtype, true, a, c->side);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+  if (e == cudaSuccess) e = launch_bulk(c->cfg.dtype, a, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+  c->launches += 2;
+  return e;
+}
+
 vplbm_status one_step(vplbm_ctx *c, cudaStream_t s) {
-  const StepArgs a = step_args(c, c->cur, sim_due(c, c->steps));
-  VPLBM_CUDA(c, launch_step(c->cfg.dtype, !c->pre, a, s));
-  ++c->launches;
+  VPLBM_CUDA(c, queue_step(c, s, c->cur, c->pre, sim_due(c, c->steps)));
   c->cur = 1 - c->cur;
   c->pre = false;
   ++c->steps;
@@ -308,10 +346,10 @@ vplbm_status ensure_graph(vplbm_ctx *c) {
   cudaGraph_t g = nullptr;
   VPLBM_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k) {
-    const StepArgs a = step_args(c, k & 1, c->sim_every == 1 && c->n_sim > 0);
-    e = launch_step(c->cfg.dtype, true, a, c->capture_stream);
-  }
+  const int64_t launches = c->launches;
+  for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
+    e = queue_step(c, c->capture_stream, k & 1, false, c->sim_every == 1 && c->n_sim > 0);
+  c->launches = launches;  // counted when the graph is launched
   cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
   if (e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -374,9 +412,8 @@ vplbm_status vplbm_create(const vplbm_config *cfg, void *dev_workspace, size_t b
   c->prev[0] = c->ws + lay.prev[0];
   c->prev[1] = c->ws + lay.prev[1];
   c->chi = (uint8_t *)(c->ws + lay.chi);
-  c->partials = (double *)(c->ws + lay.partials);
   c->sim_pts = (SimPoint *)(c->ws + lay.sim_pts);
-  c->sim_contrib = (double *)(c->ws + lay.sim_contrib);
+  c->acc = (unsigned long long *)(c->ws + lay.acc);
   c->sim_nodes = (int32_t *)(c->ws + lay.sim_nodes);
   c->hist = (double *)(c->ws + lay.hist);
   c->body[0] = (BodyState *)(c->ws + lay.body[0]);
@@ -407,6 +444,7 @@ vplbm_status vplbm_create(const vplbm_config *cfg, void *dev_workspace, size_t b
   L.uc_f = (float)L.uc;
   L.bf_f[0] = (float)L.bf[0];
   L.bf_f[1] = (float)L.bf[1];
+  L.has_bf = (L.bf[0] != 0.0 || L.bf[1] != 0.0) ? 1 : 0;
 
   const double tp = cfg->tau_plus;
   const double tm = cfg->collision == VPLBM_BGK ? tp : cfg->lambda_trt / (tp - 0.5) + 0.5;
@@ -425,9 +463,16 @@ vplbm_status vplbm_create(const vplbm_config *cfg, void *dev_workspace, size_t b
 
   cudaError_t e = cudaMemsetAsync(c->ws, 0, lay.total, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  // the side stream runs the special kernel (forces, edges, tail) at the
+  // highest priority so that its few blocks are dispatched ahead of the bulk
+  int prio_lo = 0, prio_hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
-    delete c;
-    return cuda_fail(nullptr, e, "clearing the workspace");
+    vplbm_destroy(c);
+    return cuda_fail(nullptr, e, "setting up the workspace and streams");
   }
   *out = c;
   return VPLBM_OK;
@@ -496,21 +541,49 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
   }
   // force region: tiles around the body (its farthest polygon point from the
   // reference point sets the extent); tile (0, 0) alone for an empty lattice
-  double extent = 0.0;
-  for (const SimPoint &p : pts)
+  double extent = 0.0, bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
+  for (const SimPoint &p : pts) {
     extent = std::max(extent, sqrt(p.dx * p.dx + p.dy * p.dy) + 0.5 * p.s);
-  const int ntx = (L.nx + kTileX - 1) / kTileX, nty = (L.ny + kTileY - 1) / kTileY;
+    bx0 = std::min(bx0, b->x_c + p.dx - 0.5 * p.s);
+    bx1 = std::max(bx1, b->x_c + p.dx + 0.5 * p.s);
+    by0 = std::min(by0, b->y_c + p.dy - 0.5 * p.s);
+    by1 = std::max(by1, b->y_c + p.dy + 0.5 * p.s);
+  }
+  const int tw = kTileX;
+  const int ntx = (L.nx + tw - 1) / tw, nty = (L.ny + kTileY - 1) / kTileY;
   ForceRegion reg{};
   if (b->kind != VPLBM_BODY_NONE) {
-    reg = make_region(L, b->x_c, b->y_c, extent, ntx, nty);
+    reg = b->moving ? make_region(L, b->x_c, b->y_c, 0.5 * b->length, ntx, nty, tw)
+                    : make_region_box(L, bx0, bx1, by0, by1, ntx, nty, tw);
     reg.error = 0;
     if (reg.count > kRegionCapacity)
       return fail(c, VPLBM_EINVAL, fmt("body too large: %d force-region tiles (capacity %d)", reg.count, kRegionCapacity));
   } else {
     reg.count = 1;
   }
+  // blocks reserved for region tiles: the region's tile count, or for a
+  // moving body the most tiles a box of its size can cover anywhere
+  int slots = reg.count;
+  if (b->kind != VPLBM_BODY_NONE && b->moving) {
+    const double span = 2.0 * (0.5 * b->length + kRegionMargin) + 3.0;
+    slots = ((int)(span / tw) + 2) * ((int)(span / kTileY) + 2);
+    slots = std::min(slots, kRegionCapacity);
+  }
+  // the constant part of the SIM sum: -(1/3) sum S_i n_i and its moment
+  // (zero for a closed polygon up to round-off), in FP64 in point order
+  double cfx = 0.0, cfy = 0.0, ctq = 0.0;
+  for (const SimPoint &p : pts) {
+    const double tx = p.s * (-1.0 / 3.0) * p.nx, ty = p.s * (-1.0 / 3.0) * p.ny;
+    cfx += tx;
+    cfy += ty;
+    ctq += p.dx * ty - p.dy * tx;
+  }
+  c->sim_const[0] = cfx;
+  c->sim_const[1] = cfy;
+  c->sim_const[2] = ctq;
   c->body_cfg = *b;
   c->body_host = bs;
+  c->region_slots = std::max(1, slots);
   c->n_sim = n_sim;
   c->sim_every = (b->moving && b->estimator == VPLBM_SIM) ? 1 : c->cfg.sim_every;
   if (c->graph) {
@@ -557,7 +630,7 @@ vplbm_status vplbm_step(vplbm_ctx *c, int32_t nsteps) {
     if (graphable && !c->pre && c->cur == 0 && left >= 2 * kGraphPairs) {
       if (vplbm_status st = ensure_graph(c)) return st;
       VPLBM_CUDA(c, cudaGraphLaunch(c->graph, s));
-      c->launches += 2 * kGraphPairs;
+      c->launches += 4 * kGraphPairs;
       c->steps += 2 * kGraphPairs;
       left -= 2 * kGraphPairs;
       continue;
@@ -749,6 +822,9 @@ void vplbm_destroy(vplbm_ctx *c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
 }
 

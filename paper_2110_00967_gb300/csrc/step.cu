@@ -1,59 +1,88 @@
-// step.cu -- the fused VP-LBM time step for sm_103a.
+// step.cu -- the VP-LBM time step for sm_103a.
 //
-// One launch advances the lattice by one time step and produces that step's
-// forces.  Blocks are of three kinds:
-//   * SIM blocks (the first few, when SIM is due): one integration point per
-//     thread -- the stress of Sec. 2.3.2 at the sampled fluid node from its
-//     pre-collision populations, then S_i sigma n_i and its moment (Eq. defFf),
-//     stored per point;
-//   * lattice tiles (128 x 2 nodes, one node per thread): pull-stream the
-//     pre-collision populations (Eq. eqBd with the side conditions of Sec. 3.1
-//     and 3.2), moments and penalized velocity (Eqs. updatestep ..
-//     updatestepm), force density G, equilibrium and BGK/TRT collision with
-//     the forcing term (Eq. TRT), store;
-//   * tiles of the force region (around the body) additionally sum the MEM
-//     link terms of their interface nodes (Eq. MMEL, Eq. fluidtorque) in FP64
-//     into one partial per tile.
-// The SIM blocks and the force-region tiles take a ticket when done; the last
-// of them sums the partials and the SIM entries in a fixed order in FP64,
-// records the step's forces and, for a moving body, applies the FP64
-// rigid-body update (Eqs. dep1, theta2) and re-rasterises the mask.  Every
-// other block only streams and collides: no barrier, no atomic, no FP64.
+// One time step is two launches that write disjoint nodes:
+//   * the special kernel: the SIM points (stress of Sec. 2.3.2 at the
+//     sampled fluid node from its pre-collision populations, S_i sigma n_i
+//     and its moment, Eq. defFf), the nodes on the lattice edges (side
+//     conditions of Sec. 3.1/3.2), and the tiles of the force region around
+//     the body (penalized nodes and the MEM link terms of Eq. MMEL /
+//     Eq. fluidtorque).  Its SIM and region blocks add their force terms into
+//     exact fixed-point sums and take a ticket; the last of them records the
+//     step's forces and, for a moving body, applies the FP64 rigid-body update
+//     (Eqs. dep1, theta2) and re-rasterises the mask.
+//   * the bulk kernel: every other node -- pull streaming (Eq. eqBd) and the
+//     BGK/TRT collision (Eq. TRT) of fluid nodes whose sources all lie inside
+//     the lattice; no mask, no side conditions, no forces.
+// For the first step after a pre-collision state the special kernel updates
+// every tile.
 #include "vplbm_internal.cuh"
-
-// resident blocks per SM the register allocation is sized for (80 registers)
-#ifndef VPLBM_STEP_MIN_BLOCKS
-#define VPLBM_STEP_MIN_BLOCKS 3
-#endif
 
 namespace vplbm {
 
 namespace {
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
-  // fixed-order block reduction: warp butterfly, then warp 0 over warp sums
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int nwarps = (blockDim.x * blockDim.y) >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (warp == 0) {
-    r = lane < nwarps ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// exact force sums
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FixAcc {
+  long long f[3][Fix<T>::kWords];
+  __device__ __forceinline__ FixAcc() {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int k = 0; k < Fix<T>::kWords; ++k) f[q][k] = 0;
   }
-  __syncthreads();
-  return r;  // valid in thread 0
+  __device__ __forceinline__ void add(int q, T v) {
+    long long w[Fix<T>::kWords];
+    Fix<T>::split(v, w);
+#pragma unroll
+    for (int k = 0; k < Fix<T>::kWords; ++k) f[q][k] += w[k];
+  }
+};
+
+// adds the warp's fixed-point words into acc[slot][word] for the three
+// quantities starting at slot base
+template <typename T>
+__device__ __forceinline__ void warp_add(const FixAcc<T> &a, unsigned long long *acc, int base) {
+  constexpr int W = Fix<T>::kWords;
+  long long v[3][W];
+  long long any = 0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      v[q][k] = a.f[q][k];
+      any |= v[q][k];
+    }
+  if (!__any_sync(kFull, any != 0)) return;
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+      for (int o = 16; o > 0; o >>= 1) v[q][k] += __shfl_xor_sync(kFull, v[q][k], o);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int k = 0; k < W; ++k)
+        if (v[q][k]) atomicAdd(acc + 2 * (base + q) + k, (unsigned long long)v[q][k]);
+  }
 }
 
-// Deviatoric-plus-density part of the stress of Sec. 2.3.2 at a fluid node,
+// ---------------------------------------------------------------------------
+// SIM (Sec. 2.3.2)
+// ---------------------------------------------------------------------------
+
+// The part of the stress beyond -(1/3) I at a fluid node,
 // sigma + (1/3) I = -(rho - 1)/3 I - (1 - 1/(2 tau+)) sum c c (f - feq),
-// from the pre-collision offsets, in the compute type (all terms are small).
+// from its pre-collision offsets, in the compute type (all terms are small).
 template <typename S, bool kGather>
-__device__ void node_stress(const S *buf, const typename Store<S>::T *prev, const Lattice &L,
-                            double tau_plus, int i, int j, typename Store<S>::T sig[3]) {
+__device__ __forceinline__ void node_stress(const S *buf, const typename Store<S>::T *prev,
+                                            const Lattice &L, typename Store<S>::T s, int i,
+                                            int j, typename Store<S>::T sig[3]) {
   using T = typename Store<S>::T;
   T h[9];
 #pragma unroll
@@ -79,79 +108,59 @@ __device__ void node_stress(const S *buf, const typename Store<S>::T *prev, cons
     pxy += (T)(cx_of(a) * cy_of(a)) * d;
     pyy += (T)(cy_of(a) * cy_of(a)) * d;
   }
-  const T s = (T)(1.0 - 0.5 / tau_plus);
   sig[0] = -drho / (T)3 - s * pxx;
   sig[1] = -s * pxy;
   sig[2] = -drho / (T)3 - s * pyy;
 }
 
-// pre-collision populations of an edge node, with the side conditions (kept
-// out of line: only edge nodes take this path)
-template <typename S, bool kGather>
-__device__ __noinline__ void edge_pops(const S *src, const typename Store<S>::T *prev,
-                                       const Lattice &L, int i, int j,
-                                       typename Store<S>::T *h) {
-#pragma unroll
-  for (int a = 0; a < 9; ++a) h[a] = pre_pop<S, kGather>(src, prev, L, a, i, j);
-}
-
-// MEM link terms of one interface node (Eq. MMEL, Eq. fluidtorque), FP64,
-// from its post-collision populations just stored (kept out of line: only
-// interface nodes of the force region take this path)
-template <typename S>
-__device__ __noinline__ void mem_terms(const StepArgs &p, const S *dst, int i, int j,
-                                       uint8_t m, double acc[3]) {
-  const Lattice &L = p.L;
-  const BodyState &b = *p.body_src;
-  const int64_t node = (int64_t)j * L.pitch + i;
-  const bool solid = m & kSolid;
-#pragma unroll
-  for (int a = 1; a < 9; ++a) {
-    int ni, nj;
-    if (!neighbour(L, a, i, j, ni, nj)) continue;
-    const bool nsolid = p.chi[(int64_t)nj * L.pitch + ni] & kSolid;
-    if (nsolid == solid) continue;
-    // link midpoint x_Gamma and the wall velocity u_Gamma there
-    const double xgam = (double)i + 0.5 * cx_of(a), ygam = (double)j + 0.5 * cy_of(a);
-    const double ugx = b.ux - b.omega * (ygam - b.yg);
-    const double ugy = b.uy + b.omega * (xgam - b.xg);
-    // the node's own store of this launch: read back through L2, not the
-    // read-only path
-    const double fa = (double)Store<S>::ld_own(dst + (int64_t)a * L.plane + node) + w_of(a);
-    const double sg = solid ? -1.0 : 1.0;
-    const double lx = sg * (cx_of(a) - ugx) * fa;
-    const double ly = sg * (cy_of(a) - ugy) * fa;
-    acc[0] += lx;
-    acc[1] += ly;
-    acc[2] += (xgam - b.xg) * ly - (ygam - b.yg) * lx;
-  }
-}
-
+// first fluid node of q_k = (qi, qj) + k c_a, k = 0..3, inside the lattice
+// (the four mask bytes are loaded together)
 __device__ __forceinline__ bool sim_walk(const Lattice &L, const uint8_t *chi, int a, int qi,
                                          int qj, int &oi, int &oj) {
-#pragma unroll 1
-  for (int k = 0; k <= 3; ++k) {
+  uint8_t m[4];
+  bool in[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
     const int ii = qi + k * cx_of(a), jj = qj + k * cy_of(a);
-    if (ii < 0 || ii >= L.nx || jj < 0 || jj >= L.ny) return false;
-    if (!(chi[(int64_t)jj * L.pitch + ii] & kSolid)) {
-      oi = ii;
-      oj = jj;
+    in[k] = ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny;
+    m[k] = in[k] ? chi[(int64_t)jj * L.pitch + ii] : (uint8_t)kSolid;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!in[k]) return false;
+    if (!(m[k] & kSolid)) {
+      oi = qi + k * cx_of(a);
+      oj = qj + k * cy_of(a);
       return true;
     }
   }
   return false;
 }
 
+template <typename T>
+__device__ __forceinline__ void sim_geom(const SimPoint &sp, T &dx, T &dy, T &nx, T &ny, T &s);
+template <>
+__device__ __forceinline__ void sim_geom<double>(const SimPoint &sp, double &dx, double &dy,
+                                                 double &nx, double &ny, double &s) {
+  dx = sp.dx; dy = sp.dy; nx = sp.nx; ny = sp.ny; s = sp.s;
+}
+template <>
+__device__ __forceinline__ void sim_geom<float>(const SimPoint &sp, float &dx, float &dy,
+                                                float &nx, float &ny, float &s) {
+  dx = sp.f_dx; dy = sp.f_dy; nx = sp.f_nx; ny = sp.f_ny; s = sp.f_s;
+}
+
 // One SIM integration point: the nearest node (both nodes when the point lies
-// exactly half-way), the walk along the direction closest to the normal to the
-// first fluid node, sigma averaged over the candidates, then S sigma n and its
-// moment about the reference point in FP64.
+// exactly half-way: the coordinates are compared in FP64), the walk along the
+// direction closest to the normal to the first fluid node, the stress
+// averaged over the candidates, then S (sigma + I/3) n and its moment; the
+// -(1/3) S n part sums to a constant of the polygon added in the tail.
 template <typename S, bool kGather>
-__device__ __noinline__ void sim_point(const StepArgs &p, const S *buf, const BodyState &b,
-                                       int q) {
+__device__ __noinline__ FixAcc<typename Store<S>::T> sim_point(const StepArgs &p, const S *buf, double bxg, double byg,
+                                         int q, bool &missing) {
   using T = typename Store<S>::T;
   const SimPoint sp = p.sim_pts[q];
-  const double x = b.xg + sp.dx, y = b.yg + sp.dy;
+  const double x = bxg + sp.dx, y = byg + sp.dy;
   const double rx = floor(x + 0.5), ry = floor(y + 0.5);
   const int ncx = (rx == x + 0.5) ? 2 : 1, ncy = (ry == y + 0.5) ? 2 : 1;
   const T *prev = static_cast<const T *>(p.prev_src);
@@ -167,29 +176,69 @@ __device__ __noinline__ void sim_point(const StepArgs &p, const S *buf, const Bo
       }
       if (first < 0) first = qj * p.L.nx + qi;
       T s3[3];
-      node_stress<S, kGather>(buf, prev, p.L, p.tau_plus, qi, qj, s3);
+      node_stress<S, kGather>(buf, prev, p.L, Consts<T>(p).sim_s, qi, qj, s3);
       sig[0] += s3[0];
       sig[1] += s3[1];
       sig[2] += s3[2];
     }
-  double *out = p.sim_contrib + 3 * (int64_t)q;
-  if (!ok) {
-    p.sim_nodes[q] = -1;
-    out[0] = out[1] = out[2] = 0.0;
-    return;
-  }
-  const double cnt = (double)(ncx * ncy);
-  // sigma = -(1/3) I + (the small part); the constant part in FP64
-  const double sxx = (double)sig[0] / cnt - 1.0 / 3.0;
-  const double sxy = (double)sig[1] / cnt;
-  const double syy = (double)sig[2] / cnt - 1.0 / 3.0;
-  const double tx = sp.s * (sxx * sp.nx + sxy * sp.ny);
-  const double ty = sp.s * (sxy * sp.nx + syy * sp.ny);
-  p.sim_nodes[q] = first;
-  out[0] = tx;
-  out[1] = ty;
-  out[2] = sp.dx * ty - sp.dy * tx;
+  p.sim_nodes[q] = ok ? first : -1;
+  missing = !ok;
+  FixAcc<T> r;
+  if (!ok) return r;
+  // mean over 1, 2 or 4 candidates: an exact power-of-two scaling
+  const T inv = (ncx * ncy == 1) ? (T)1 : ((ncx * ncy == 2) ? (T)0.5 : (T)0.25);
+  T dx, dy, nx, ny, sl;
+  sim_geom<T>(sp, dx, dy, nx, ny, sl);
+  const T sxx = sig[0] * inv, sxy = sig[1] * inv, syy = sig[2] * inv;
+  const T tx = sl * (sxx * nx + sxy * ny);
+  const T ty = sl * (sxy * nx + syy * ny);
+  r.add(0, tx);
+  r.add(1, ty);
+  r.add(2, dx * ty - dy * tx);
+  return r;
 }
+
+// ---------------------------------------------------------------------------
+// MEM (Sec. 2.3.1)
+// ---------------------------------------------------------------------------
+
+// The link terms of one interface node (Eq. MMEL): for each lattice
+// neighbour of the other phase, the fluid end adds (c_a - u_Gamma) f~_a and
+// the solid end subtracts its own (c_a - u_Gamma) f~_a, with x_Gamma the link
+// midpoint and u_Gamma the rigid velocity there; torques about the reference
+// point (Eq. fluidtorque).  f~ = h~ + w is split so that the w parts, which
+// cancel in pairs around a fixed body, are rounded exactly.
+template <typename T>
+__device__ __forceinline__ void mem_terms(const StepArgs &p, const T (&o)[9], int i, int j,
+                                          uint8_t m, FixAcc<T> &acc) {
+  const Lattice &L = p.L;
+  const BodyRef<T> b(*p.body_src);
+  const bool solid = m & kSolid;
+  const T sg = solid ? (T)-1 : (T)1;
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    int ni, nj;
+    if (!neighbour(L, a, i, j, ni, nj)) continue;
+    const bool nsolid = p.chi[(int64_t)nj * L.pitch + ni] & kSolid;
+    if (nsolid == solid) continue;
+    const T rx = ((T)i - b.xg) + (T)(0.5 * cx_of(a));
+    const T ry = ((T)j - b.yg) + (T)(0.5 * cy_of(a));
+    const T vx = (T)cx_of(a) - (b.ux - b.om * ry);
+    const T vy = (T)cy_of(a) - (b.uy + b.om * rx);
+    const T ah = sg * o[a], aw = sg * (T)w_of(a);
+    const T lxh = vx * ah, lyh = vy * ah, lxw = vx * aw, lyw = vy * aw;
+    acc.add(0, lxh);
+    acc.add(0, lxw);
+    acc.add(1, lyh);
+    acc.add(1, lyw);
+    acc.add(2, rx * lyh - ry * lxh);
+    acc.add(2, rx * lyw - ry * lxw);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// rigid body and the tail
+// ---------------------------------------------------------------------------
 
 // Rigid-body update (Eqs. dep1 and theta2, explicit trapezoid in time) for a
 // disk of density ratio rho_s/rho in a fluid of density 1.
@@ -244,38 +293,25 @@ __device__ void tail_reraster(const StepArgs &p, const BodyState &old_b, const B
   }
 }
 
-// The last participating block: FP64 sums in a fixed order, histories, body.
-__device__ void tail(const StepArgs &p, const ForceRegion &reg, double *red) {
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
-  __shared__ double tot[6];
+// The last participating block: the step's forces from the fixed-point sums
+// (plus the polygon's constant SIM part), histories, running sums, body.
+template <typename T>
+__device__ void tail(const StepArgs &p, const ForceRegion &reg) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  __shared__ double tot[kAccSlots];
   __shared__ BodyState old_b, new_b;
-  // partials and SIM entries were written by other SMs: read them through L2
-  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
-  for (int k = tid; k < reg.count; k += nt) {
-    m0 += __ldcg(p.mem_partials + 3 * k + 0);
-    m1 += __ldcg(p.mem_partials + 3 * k + 1);
-    m2 += __ldcg(p.mem_partials + 3 * k + 2);
-  }
   const bool do_sim = p.sim_blocks > 0;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  int missing = 0;
-  if (do_sim) {
-    for (int q = tid; q < p.n_sim; q += nt) {
-      s0 += __ldcg(p.sim_contrib + 3 * q + 0);
-      s1 += __ldcg(p.sim_contrib + 3 * q + 1);
-      s2 += __ldcg(p.sim_contrib + 3 * q + 2);
-      missing |= __ldcg(p.sim_nodes + q) < 0;
-    }
-  }
-  missing = __syncthreads_or(missing);
-  const double v[6] = {m0, m1, m2, s0, s1, s2};
-  for (int k = 0; k < 6; ++k) {
-    const double r = block_sum(v[k], red);
-    if (tid == 0) tot[k] = r;
+  if (tid < kAccSlots) {
+    // the sums were added by other SMs: read them through L2
+    const long long w0 = (long long)__ldcg(p.acc + 2 * tid);
+    const long long w1 = (long long)__ldcg(p.acc + 2 * tid + 1);
+    double v = Fix<T>::value(w0, w1);
+    if (tid >= 3) v += p.sim_const[tid - 3];
+    tot[tid] = v;
   }
   __syncthreads();
-  const long long step = *p.dev_step;
   if (tid == 0) {
+    const long long step = *p.dev_step;
     double *h = p.hist + 6 * (step % p.hist_len);
     for (int k = 0; k < 3; ++k) h[k] = tot[k];
     for (int k = 3; k < 6; ++k) h[k] = do_sim ? tot[k] : __longlong_as_double(0x7ff8000000000000LL);
@@ -284,7 +320,6 @@ __device__ void tail(const StepArgs &p, const ForceRegion &reg, double *red) {
     if (do_sim) {
       for (int k = 3; k < 6; ++k) p.sums[k] += tot[k];
       p.counts[1] += 1;
-      if (missing) atomicOr(p.status, kStatusSimMissing);
     }
     old_b = *p.body_src;
     new_b = old_b;
@@ -293,8 +328,9 @@ __device__ void tail(const StepArgs &p, const ForceRegion &reg, double *red) {
       const bool sim = old_b.estimator == VPLBM_SIM;
       const double F[3] = {sim ? tot[3] : tot[0], sim ? tot[4] : tot[1], sim ? tot[5] : tot[2]};
       rigid_update(new_b, F);
-      nreg = make_region(p.L, new_b.xg, new_b.yg, 0.5 * new_b.length, p.ntiles_x, p.ntiles_y);
-      if (nreg.error || nreg.count > p.region_capacity ||
+      nreg = make_region(p.L, new_b.xg, new_b.yg, 0.5 * new_b.length, p.ntiles_x, p.ntiles_y,
+                         p.tile_w);
+      if (nreg.error || nreg.count > p.region_slots || nreg.count > p.region_capacity ||
           fabs(new_b.xg - old_b.xg) >= 1.0 || fabs(new_b.yg - old_b.yg) >= 1.0) {
         // the body left the lattice or moved a node in one step: keep it
         // where it was and flag the run as unstable
@@ -305,137 +341,209 @@ __device__ void tail(const StepArgs &p, const ForceRegion &reg, double *red) {
     }
     *p.body_dst = new_b;
     *p.reg_dst = nreg;
+    *p.dev_step = step + 1;
   }
   __syncthreads();
   if (old_b.moving && (new_b.xg != old_b.xg || new_b.yg != old_b.yg)) tail_reraster(p, old_b, new_b);
   __syncthreads();
+  if (tid < kAccWords) p.acc[tid] = 0ull;
+  __syncthreads();
   if (tid == 0) {
-    *p.dev_step = step + 1;
     __threadfence();
     *p.ticket = 0u;
   }
 }
 
+// ---------------------------------------------------------------------------
+// node update
+// ---------------------------------------------------------------------------
+
+// BGK/TRT collision with the forcing term (Eq. TRT) of one node from its
+// moments, into o.  kForce = false drops the forcing term (G = 0: a fluid
+// node without body force).
+template <typename T, bool kForce>
+__device__ __forceinline__ void collide(const T (&h)[9], T drho, T rho, T ux, T uy, T gx, T gy,
+                                        const Consts<T> &c, T (&o)[9]) {
+  const T uu = ux * ux + uy * uy;
+  const T ug = kForce ? ux * gx + uy * gy : (T)0;
+  {
+    const T w0 = (T)w_of(0);
+    const T heq0 = w0 * (drho - (T)1.5 * rho * uu);
+    T r = h[0] - c.s_plus * (h[0] - heq0);
+    if (kForce) r += c.a_plus * (w0 * ((T)-3 * ug));
+    o[0] = r;
+  }
+#pragma unroll
+  for (int a = 1; a <= 6; ++a) {
+    if (a == 3 || a == 4) continue;
+    const int b = opp_of(a);
+    const T w = (T)w_of(a);
+    const T cu = (T)cx_of(a) * ux + (T)cy_of(a) * uy;
+    const T heqp = w * (drho + rho * ((T)4.5 * cu * cu - (T)1.5 * uu));
+    const T heqm = w * (T)3 * rho * cu;
+    const T hp = (T)0.5 * (h[a] + h[b]);
+    const T hm = (T)0.5 * (h[a] - h[b]);
+    T dp = -c.s_plus * (hp - heqp);
+    T dm = -c.s_minus * (hm - heqm);
+    if (kForce) {
+      const T cg = (T)cx_of(a) * gx + (T)cy_of(a) * gy;
+      dp += c.a_plus * (w * ((T)9 * cu * cg - (T)3 * ug));
+      dm += c.a_minus * (w * (T)3 * cg);
+    }
+    o[a] = h[a] + dp + dm;
+    o[b] = h[b] + dp - dm;
+  }
+}
+
+// Moments, penalized velocity and force density of one node (Eqs. updatestep
+// .. updatestepm: G = -rho (chi/eta)(u - u_s) in the rearranged form
+// -(chi/eta)(j - rho u_s)/(1 + chi dt/(2 eta)), plus the body force), then
+// the collision.  Returns true for a non-finite or non-positive density.
+template <typename T>
+__device__ __forceinline__ bool update_node(const T (&h)[9], uint8_t m, int i, int j,
+                                            const Lattice &L, const BodyState *body,
+                                            const Consts<T> &cst, T (&o)[9]) {
+  const T drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+  const T rho = (T)1 + drho;
+  T jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+  T jy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
+  if ((m & kSolid) || L.has_bf) {
+    const T bfx = lat_bf<T>(L, 0), bfy = lat_bf<T>(L, 1);
+    jx += (T)0.5 * bfx;
+    jy += (T)0.5 * bfy;
+    T ux, uy, gx = bfx, gy = bfy;
+    if (m & kSolid) {
+      T usx, usy;
+      solid_velocity<T>(*body, i, j, usx, usy);
+      const T k = cst.half_pen;
+      const T den = rho + k * rho;
+      ux = (jx + k * rho * usx) / den;
+      uy = (jy + k * rho * usy) / den;
+      const T pen = (T)2 * k;
+      gx -= pen * (jx - rho * usx) / ((T)1 + k);
+      gy -= pen * (jy - rho * usy) / ((T)1 + k);
+    } else {
+      const T inv = (T)1 / rho;
+      ux = jx * inv;
+      uy = jy * inv;
+    }
+    collide<T, true>(h, drho, rho, ux, uy, gx, gy, cst, o);
+  } else {
+    const T inv = (T)1 / rho;
+    collide<T, false>(h, drho, rho, jx * inv, jy * inv, (T)0, (T)0, cst, o);
+  }
+  return !(rho > (T)0) || !isfinite(rho);
+}
+
+// pre-collision populations of an edge node, with the side conditions
 template <typename S, bool kGather>
-__global__ void __launch_bounds__(kThreads, VPLBM_STEP_MIN_BLOCKS) step_kernel(const StepArgs p) {
+__device__ __forceinline__ void edge_pops(const S *src, const typename Store<S>::T *prev,
+                                          const Lattice &L, int i, int j,
+                                          typename Store<S>::T (&h)[9]) {
+#pragma unroll
+  for (int a = 0; a < 9; ++a) h[a] = pre_pop<S, kGather>(src, prev, L, a, i, j);
+}
+
+// One node of the special kernel: pull (with the side conditions where
+// needed), keep the outlet column, update, store, and the MEM link terms of
+// an interface node of the force region.
+template <typename S, bool kGather>
+__device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bool in_reg,
+                                             FixAcc<typename Store<S>::T> &acc) {
   using T = typename Store<S>::T;
-  __shared__ double red[32];
-  __shared__ int is_last;
   const Lattice &L = p.L;
   const S *__restrict__ src = static_cast<const S *>(p.src);
+  S *dst = static_cast<S *>(p.dst);
+  const T *prev = static_cast<const T *>(p.prev_src);
+  const int64_t node = (int64_t)j * L.pitch + i;
+  T h[9];
+  if (kGather && i > 0 && i < L.nx - 1 && j > 0 && j < L.ny - 1) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a)
+      h[a] = Store<S>::ld(src + (int64_t)a * L.plane + node - cy_of(a) * L.pitch - cx_of(a));
+  } else {
+    edge_pops<S, kGather>(src, prev, L, i, j, h);
+  }
+  if (i == L.nx - 1 && L.bc[1] == VPLBM_OUTLET_CONVECTIVE) {
+    // the outlet column's pre-collision values, for the next step
+    T *pd = static_cast<T *>(p.prev_dst);
+    pd[0 * L.ny + j] = h[3];
+    pd[1 * L.ny + j] = h[6];
+    pd[2 * L.ny + j] = h[7];
+  }
+  const uint8_t m = p.chi[node];
+  T o[9];
+  const bool bad = update_node<T>(h, m, i, j, L, p.body_src, Consts<T>(p), o);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) Store<S>::st(dst + (int64_t)a * L.plane + node, o[a]);
+  if (in_reg && (m & kInterface)) mem_terms<T>(p, o, i, j, m, acc);
+  return bad;
+}
+
+// ---------------------------------------------------------------------------
+// special kernel: SIM blocks, then blocks of edge nodes, then the
+// force-region tiles (or, for the first step, every tile)
+// ---------------------------------------------------------------------------
+template <typename S, bool kGather>
+__global__ void __launch_bounds__(kThreads) special_kernel(const StepArgs p) {
+  using T = typename Store<S>::T;
+  __shared__ int is_last;
+  const Lattice &L = p.L;
   const int tid = threadIdx.y * kTileX + threadIdx.x;
   const ForceRegion reg = *p.reg_src;
+  const int b = blockIdx.x;
 
-  if ((int)blockIdx.x < p.sim_blocks) {
+  if (b < p.sim_blocks) {
     // ---- SIM points of this level ----
-    const BodyState b = *p.body_src;
-    const int q = blockIdx.x * kThreads + tid;
-    if (q < p.n_sim) sim_point<S, kGather>(p, src, b, q);
+    const int q = b * kThreads + tid;
+    FixAcc<T> acc;
+    bool missing = false;
+    if (q < p.n_sim) {
+      const BodyState *body = p.body_src;
+      acc = sim_point<S, kGather>(p, static_cast<const S *>(p.src), body->xg, body->yg, q,
+                                  missing);
+    }
+    if (__any_sync(kFull, missing) && (tid & 31) == 0) atomicOr(p.status, kStatusSimMissing);
+    warp_add(acc, p.acc, 3);
+  } else if (!p.all_tiles && b < p.sim_blocks + p.edge_blocks) {
+    // ---- one edge node per thread (nodes of force-region tiles excluded) ----
+    const int e = (b - p.sim_blocks) * kThreads + tid;
+    bool bad = false;
+    if (e < p.n_edge) {
+      int i, j;
+      edge_node(e, L.nx, L.ny, i, j);
+      const int ti = i / kTileX, tj = j / kTileY;
+      const bool in_reg = ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1;
+      if (!in_reg) {
+        FixAcc<T> unused;
+        bad = special_node<S, kGather>(p, i, j, false, unused);
+      }
+    }
+    if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(p.status, kStatusUnstable);
+    return;
   } else {
-    const int t = blockIdx.x - p.sim_blocks;
-    const int ti = t % p.ntiles_x, tj = t / p.ntiles_x;
+    // ---- a whole tile: every tile (first step) or a force-region tile ----
+    int ti, tj;
+    const int r = b - p.sim_blocks;
+    if (p.all_tiles) {
+      ti = r % p.ntiles_x;
+      tj = r / p.ntiles_x;
+    } else {
+      const int k = r - p.edge_blocks;
+      if (k >= reg.count) return;  // spare slot (moving bodies)
+      const int rw = reg.ti1 - reg.ti0 + 1;
+      ti = reg.ti0 + k % rw;
+      tj = reg.tj0 + k / rw;
+    }
     const bool in_reg = ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1;
     const int i = ti * kTileX + threadIdx.x;
     const int j = tj * kTileY + threadIdx.y;
-    const bool valid = i < L.nx && j < L.ny;
     bool bad = false;
-    double macc[3] = {0.0, 0.0, 0.0};
-    if (valid) {
-      S *dst = static_cast<S *>(p.dst);
-      const T *prev = static_cast<const T *>(p.prev_src);
-      const int64_t node = (int64_t)j * L.pitch + i;
-
-      // ---- streaming (pull) ----
-      T h[9];
-      if (kGather && i > 0 && i < L.nx - 1 && j > 0 && j < L.ny - 1) {
-#pragma unroll
-        for (int a = 0; a < 9; ++a)
-          h[a] = Store<S>::ld(src + (int64_t)a * L.plane + node - cy_of(a) * L.pitch - cx_of(a));
-      } else {
-        edge_pops<S, kGather>(src, prev, L, i, j, h);
-      }
-      if (i == L.nx - 1 && L.bc[1] == VPLBM_OUTLET_CONVECTIVE) {
-        T *pd = static_cast<T *>(p.prev_dst);
-        pd[0 * L.ny + j] = h[3];
-        pd[1 * L.ny + j] = h[6];
-        pd[2 * L.ny + j] = h[7];
-      }
-
-      // ---- moments and penalized velocity ----
-      const T drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-      const T rho = (T)1 + drho;
-      const T bfx = lat_bf<T>(L, 0), bfy = lat_bf<T>(L, 1);
-      T jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
-      T jy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
-      jx += (T)0.5 * bfx;
-      jy += (T)0.5 * bfy;
-      const uint8_t m = p.chi[node];
-      T ux, uy, gx = bfx, gy = bfy;
-      if (m & kSolid) {
-        T usx, usy;
-        solid_velocity<T>(*p.body_src, i, j, usx, usy);
-        const T k = (T)p.half_pen;
-        const T den = rho + k * rho;
-        ux = (jx + k * rho * usx) / den;
-        uy = (jy + k * rho * usy) / den;
-        const T pen = (T)2 * k;
-        gx -= pen * (jx - rho * usx) / ((T)1 + k);
-        gy -= pen * (jy - rho * usy) / ((T)1 + k);
-      } else {
-        const T inv = (T)1 / rho;
-        ux = jx * inv;
-        uy = jy * inv;
-      }
-      bad = !(rho > (T)0) || !isfinite(rho);
-
-      // ---- collision (BGK / TRT with the forcing term) ----
-      const T s_plus = (T)p.s_plus, s_minus = (T)p.s_minus;
-      const T a_plus = (T)p.a_plus, a_minus = (T)p.a_minus;
-      const T uu = ux * ux + uy * uy;
-      const T ug = ux * gx + uy * gy;
-      T ht[9];
-      {
-        const T w0 = (T)w_of(0);
-        const T heq0 = w0 * (drho - (T)1.5 * rho * uu);
-        const T f0 = w0 * ((T)-3 * ug);
-        ht[0] = h[0] - s_plus * (h[0] - heq0) + a_plus * f0;
-      }
-#pragma unroll
-      for (int a = 1; a <= 6; ++a) {
-        if (a == 3 || a == 4) continue;
-        const int o = opp_of(a);
-        const T w = (T)w_of(a);
-        const T cu = (T)cx_of(a) * ux + (T)cy_of(a) * uy;
-        const T cg = (T)cx_of(a) * gx + (T)cy_of(a) * gy;
-        const T heqp = w * (drho + rho * ((T)4.5 * cu * cu - (T)1.5 * uu));
-        const T heqm = w * (T)3 * rho * cu;
-        const T fp = w * ((T)9 * cu * cg - (T)3 * ug);
-        const T fm = w * (T)3 * cg;
-        const T hp = (T)0.5 * (h[a] + h[o]);
-        const T hm = (T)0.5 * (h[a] - h[o]);
-        const T dp = a_plus * fp - s_plus * (hp - heqp);
-        const T dm = a_minus * fm - s_minus * (hm - heqm);
-        ht[a] = h[a] + dp + dm;
-        ht[o] = h[o] + dp - dm;
-      }
-#pragma unroll
-      for (int a = 0; a < 9; ++a) Store<S>::st(dst + (int64_t)a * L.plane + node, ht[a]);
-
-      // ---- MEM link terms of this node ----
-      if (in_reg && (m & kInterface)) mem_terms<S>(p, dst, i, j, m, macc);
-    }
-    // instability flag, one atomic per warp that saw it
-    if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(p.status, kStatusUnstable);
+    FixAcc<T> acc;
+    if (i < L.nx && j < L.ny) bad = special_node<S, kGather>(p, i, j, in_reg, acc);
+    if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(p.status, kStatusUnstable);
     if (!in_reg) return;  // uniform over the block
-    const double r0 = block_sum(macc[0], red);
-    const double r1 = block_sum(macc[1], red);
-    const double r2 = block_sum(macc[2], red);
-    if (tid == 0) {
-      const int k = (tj - reg.tj0) * (reg.ti1 - reg.ti0 + 1) + (ti - reg.ti0);
-      p.mem_partials[3 * k + 0] = r0;
-      p.mem_partials[3 * k + 1] = r1;
-      p.mem_partials[3 * k + 2] = r2;
-    }
+    warp_add(acc, p.acc, 0);
   }
 
   // ---- ticket among the SIM blocks and the force-region tiles ----
@@ -449,25 +557,89 @@ __global__ void __launch_bounds__(kThreads, VPLBM_STEP_MIN_BLOCKS) step_kernel(c
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  tail(p, reg, red);
+  tail<T>(p, reg);
+}
+
+// ---------------------------------------------------------------------------
+// bulk kernel: every node off the lattice edges and outside the force-region
+// tiles -- fluid nodes whose pull sources all lie inside the lattice.
+// ---------------------------------------------------------------------------
+template <typename S, bool kForce>
+__global__ void __launch_bounds__(kThreads) bulk_kernel(const StepArgs p) {
+  using T = typename Store<S>::T;
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  {
+    const ForceRegion reg = *p.reg_src;
+    if (ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1) return;
+  }
+  const Lattice &L = p.L;
+  const int i = ti * kTileX + threadIdx.x;
+  const int j = tj * kTileY + threadIdx.y;
+  if (i < 1 || i > L.nx - 2 || j < 1 || j > L.ny - 2) return;  // edge nodes: special kernel
+  const S *__restrict__ src = static_cast<const S *>(p.src);
+  S *__restrict__ dst = static_cast<S *>(p.dst);
+  const int64_t node = (int64_t)j * L.pitch + i;
+  T h[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a)
+    h[a] = Store<S>::ld(src + (int64_t)a * L.plane + node - cy_of(a) * L.pitch - cx_of(a));
+  const Consts<T> cst(p);
+  const T drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+  const T rho = (T)1 + drho;
+  T jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+  T jy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
+  T o[9];
+  if (kForce) {
+    const T bfx = lat_bf<T>(L, 0), bfy = lat_bf<T>(L, 1);
+    jx += (T)0.5 * bfx;
+    jy += (T)0.5 * bfy;
+    const T inv = (T)1 / rho;
+    collide<T, true>(h, drho, rho, jx * inv, jy * inv, bfx, bfy, cst, o);
+  } else {
+    const T inv = (T)1 / rho;
+    collide<T, false>(h, drho, rho, jx * inv, jy * inv, (T)0, (T)0, cst, o);
+  }
+#pragma unroll
+  for (int a = 0; a < 9; ++a) Store<S>::st(dst + (int64_t)a * L.plane + node, o[a]);
+  if (!(rho > (T)0) || !isfinite(rho)) atomicOr(p.status, kStatusUnstable);
 }
 
 template <typename S, bool kGather>
-cudaError_t launch_t(const StepArgs &a, cudaStream_t s) {
-  const int grid = a.sim_blocks + a.ntiles_x * a.ntiles_y;
-  step_kernel<S, kGather><<<grid, dim3(kTileX, kTileY), 0, s>>>(a);
+cudaError_t special_t(const StepArgs &a, cudaStream_t s) {
+  const int tiles = a.all_tiles ? a.ntiles_x * a.ntiles_y : a.edge_blocks + a.region_slots;
+  special_kernel<S, kGather><<<a.sim_blocks + tiles, dim3(kTileX, kTileY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t bulk_t(const StepArgs &a, cudaStream_t s) {
+  const dim3 grid(a.ntiles_x, a.ntiles_y);
+  if (a.L.has_bf)
+    bulk_kernel<S, true><<<grid, dim3(kTileX, kTileY), 0, s>>>(a);
+  else
+    bulk_kernel<S, false><<<grid, dim3(kTileX, kTileY), 0, s>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_step(int dtype, bool gather, const StepArgs &a, cudaStream_t s) {
+cudaError_t launch_special(int dtype, bool gather, const StepArgs &a, cudaStream_t s) {
   switch (dtype) {
-    case VPLBM_F64: return gather ? launch_t<double, true>(a, s) : launch_t<double, false>(a, s);
-    case VPLBM_F32: return gather ? launch_t<float, true>(a, s) : launch_t<float, false>(a, s);
-    case VPLBM_F16_OFS: return gather ? launch_t<__half, true>(a, s) : launch_t<__half, false>(a, s);
+    case VPLBM_F64: return gather ? special_t<double, true>(a, s) : special_t<double, false>(a, s);
+    case VPLBM_F32: return gather ? special_t<float, true>(a, s) : special_t<float, false>(a, s);
+    case VPLBM_F16_OFS: return gather ? special_t<__half, true>(a, s) : special_t<__half, false>(a, s);
     case VPLBM_BF16_OFS:
-      return gather ? launch_t<__nv_bfloat16, true>(a, s) : launch_t<__nv_bfloat16, false>(a, s);
+      return gather ? special_t<__nv_bfloat16, true>(a, s) : special_t<__nv_bfloat16, false>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bulk(int dtype, const StepArgs &a, cudaStream_t s) {
+  switch (dtype) {
+    case VPLBM_F64: return bulk_t<double>(a, s);
+    case VPLBM_F32: return bulk_t<float>(a, s);
+    case VPLBM_F16_OFS: return bulk_t<__half>(a, s);
+    case VPLBM_BF16_OFS: return bulk_t<__nv_bfloat16>(a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -37,17 +37,12 @@ __host__ __device__ __forceinline__ constexpr double w_of(int a) {
   return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
-// lattice tile of one block, one node per thread
-#ifndef VPLBM_TILE_X
-#define VPLBM_TILE_X 128
-#endif
-#ifndef VPLBM_TILE_Y
-#define VPLBM_TILE_Y 2
-#endif
-constexpr int kTileX = VPLBM_TILE_X;  // threads along x (whole warps per row)
-constexpr int kTileY = VPLBM_TILE_Y;  // rows
+// A lattice tile is one block: kTileX x kTileY nodes, one node per thread
+// (warps along x).
+constexpr int kTileX = 128;
+constexpr int kTileY = 2;
 constexpr int kThreads = kTileX * kTileY;
-constexpr int kRegionCapacity = 16384;  // force-region tiles (MEM partials)
+constexpr int kRegionCapacity = 16384;  // force-region tiles
 constexpr int kSimThreads = 128;        // threads per SIM block
 
 // mask byte bits
@@ -153,8 +148,69 @@ struct SimPoint {
   double nx, ny;  // outward unit normal
   double s;       // edge length S_i
   int32_t dir;    // lattice direction closest to the normal
-  int32_t pad;
+  float f_dx, f_dy, f_nx, f_ny, f_s;  // FP32 copies for FP32 paths
 };
+
+// body reference point and rigid velocity in the compute type
+template <typename T>
+struct BodyRef;
+template <>
+struct BodyRef<double> {
+  double xg, yg, ux, uy, om;
+  __device__ __forceinline__ explicit BodyRef(const BodyState &b)
+      : xg(b.xg), yg(b.yg), ux(b.ux), uy(b.uy), om(b.omega) {}
+};
+template <>
+struct BodyRef<float> {
+  float xg, yg, ux, uy, om;
+  __device__ __forceinline__ explicit BodyRef(const BodyState &b)
+      : xg(b.f_xg), yg(b.f_yg), ux(b.f_ux), uy(b.f_uy), om(b.f_omega) {}
+};
+
+// ---------------------------------------------------------------------------
+// Force sums are exact 64-bit fixed-point integers: each term, computed in the
+// compute type, is rounded once to a multiple of 2^-kF (forces) or 2^-kT
+// (torques) and the integers are added, which is exact and independent of
+// the order, so warps can add with integer atomics and the result is
+// reproducible bit for bit.  (FP64 arithmetic runs at about 1/58 of the FP32
+// rate on this part, so the sums avoid it; the totals are converted to FP64.)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Fix;
+template <>
+struct Fix<double> {
+  // two words: round(v 2^30) and the exact remainder at 2^-82 (|sum| < 2^33)
+  static constexpr int kWords = 2;
+  static __device__ __forceinline__ void split(double v, long long (&w)[2]) {
+    const long long hi = __double2ll_rn(v * 1073741824.0);              // 2^30
+    const double rem = v - (double)hi * 9.313225746154785e-10;          // exact
+    w[0] = hi;
+    w[1] = __double2ll_rn(rem * 4835703278458516698824704.0);           // 2^82
+  }
+  static __host__ __device__ double value(long long w0, long long w1) {
+    return (double)w0 * 9.313225746154785e-10 + (double)w1 * 2.0679515313825692e-25;
+  }
+};
+template <>
+struct Fix<float> {
+  // one word at 2^-40 (|sum| < 2^23); the terms carry FP32 precision anyway
+  static constexpr int kWords = 1;
+  // round(t) for an FP32 value t with |t| < 2^62, without FP64: split at 2^31
+  static __device__ __forceinline__ long long round_ll(float t) {
+    const int hi = __float2int_rz(t * 4.656612873077392578125e-10f);  // trunc(t / 2^31)
+    const float rem = t - (float)hi * 2147483648.0f;                  // exact
+    return ((long long)hi << 31) + (long long)__float2int_rn(rem);
+  }
+  static __device__ __forceinline__ void split(float v, long long (&w)[1]) {
+    w[0] = round_ll(v * 1099511627776.0f);  // 2^40
+  }
+  static __host__ __device__ double value(long long w0, long long) {
+    return (double)w0 * 9.094947017729282e-13;  // 2^-40
+  }
+};
+// accumulator words: (MEM Fx, Fy, T, SIM Fx, Fy, T) x two words
+constexpr int kAccSlots = 6;
+constexpr int kAccWords = 2 * kAccSlots;
 
 // ---------------------------------------------------------------------------
 // lattice geometry and side conditions, shared by every kernel
@@ -169,6 +225,7 @@ struct Lattice {
   float kin_f[9];    // the same in FP32 (no FP64 work on FP32 paths)
   float uc_f;
   float bf_f[2];
+  int32_t has_bf;    // body force nonzero: every node carries a forcing term
 };
 
 // lattice constants in the compute type
@@ -333,9 +390,8 @@ struct StepArgs {
   BodyState *body_dst;         // body at level n + 1 (written by the tail)
   const ForceRegion *reg_src;
   ForceRegion *reg_dst;
-  double *mem_partials;  // [region tiles][3]
+  unsigned long long *acc;  // [6][2] fixed-point sums of this step
   const SimPoint *sim_pts;
-  double *sim_contrib;   // [n_sim][3]
   int32_t *sim_nodes;    // [n_sim]
   int32_t n_sim;
   int32_t sim_blocks;    // leading blocks that evaluate SIM (0: SIM not due)
@@ -347,33 +403,86 @@ struct StepArgs {
   long long *dev_step;   // steps completed
   unsigned int *ticket;
   int32_t *status;
-  // collision constants
+  // collision constants, FP64 and FP32 copies (FP32 paths must not convert
+  // from FP64 per node: GB300 runs FP64 at a small fraction of FP32)
   double s_plus, s_minus;  // 1/tau+, 1/tau-
   double a_plus, a_minus;  // forcing prefactors
   double half_pen;         // dt/(2 eta)
   double tau_plus;
+  double sim_const[3];     // -(1/3) sum S n and its moment: the SIM constant part
+  float f_s_plus, f_s_minus, f_a_plus, f_a_minus, f_half_pen, f_sim_s;
   int32_t ntiles_x, ntiles_y;
-  int32_t region_capacity;  // capacity of mem_partials in tiles
-  int32_t pad1;
+  int32_t region_capacity;  // most force-region tiles a step may hold
+  int32_t tile_w;           // nodes along x of one tile
+  int32_t all_tiles;        // 1: the special kernel updates every tile (first step)
+  int32_t n_edge;           // nodes on the lattice edges
+  int32_t edge_blocks;      // special-kernel blocks for the edge nodes
+  int32_t region_slots;     // special-kernel blocks reserved for force-region tiles
 };
 
-// tile range of the force region of a body at (xg, yg) with radius-like extent r
-__host__ __device__ inline ForceRegion make_region(const Lattice &L, double xg, double yg,
-                                                   double r, int ntiles_x, int ntiles_y) {
+// the nodes on the lattice edges, enumerated: first row, last row, then the
+// first and the last column between them
+__host__ __device__ inline int edge_count(int nx, int ny) { return 2 * nx + 2 * (ny - 2); }
+__host__ __device__ inline void edge_node(int e, int nx, int ny, int &i, int &j) {
+  if (e < nx) {
+    i = e;
+    j = 0;
+    return;
+  }
+  e -= nx;
+  if (e < nx) {
+    i = e;
+    j = ny - 1;
+    return;
+  }
+  e -= nx;
+  if (e < ny - 2) {
+    i = 0;
+    j = 1 + e;
+    return;
+  }
+  i = nx - 1;
+  j = 1 + (e - (ny - 2));
+}
+
+// collision constants in the compute type
+template <typename T>
+struct Consts;
+template <>
+struct Consts<double> {
+  double s_plus, s_minus, a_plus, a_minus, half_pen, sim_s;
+  __device__ __forceinline__ explicit Consts(const StepArgs &p)
+      : s_plus(p.s_plus), s_minus(p.s_minus), a_plus(p.a_plus), a_minus(p.a_minus),
+        half_pen(p.half_pen), sim_s(1.0 - 0.5 / p.tau_plus) {}
+};
+template <>
+struct Consts<float> {
+  float s_plus, s_minus, a_plus, a_minus, half_pen, sim_s;
+  __device__ __forceinline__ explicit Consts(const StepArgs &p)
+      : s_plus(p.f_s_plus), s_minus(p.f_s_minus), a_plus(p.f_a_plus), a_minus(p.f_a_minus),
+        half_pen(p.f_half_pen), sim_s(p.f_sim_s) {}
+};
+
+// tile range of the force region of a body whose bounding box is
+// [x0, x1] x [y0, y1], widened by kRegionMargin nodes
+__host__ __device__ inline ForceRegion make_region_box(const Lattice &L, double x0, double x1,
+                                                       double y0, double y1, int ntiles_x,
+                                                       int ntiles_y, int tile_w) {
   ForceRegion g{};
-  const double m = r + kRegionMargin;
-  int i0 = (int)floor(xg - m), i1 = (int)ceil(xg + m);
-  int j0 = (int)floor(yg - m), j1 = (int)ceil(yg + m);
+  const double m = kRegionMargin;
+  int i0 = (int)floor(x0 - m), i1 = (int)ceil(x1 + m);
+  int j0 = (int)floor(y0 - m), j1 = (int)ceil(y1 + m);
   g.error = (i0 < -kRegionMargin || j0 < -kRegionMargin || i1 > L.nx - 1 + kRegionMargin ||
-             j1 > L.ny - 1 + kRegionMargin || !(xg == xg) || !(yg == yg))
+             j1 > L.ny - 1 + kRegionMargin || !(x0 == x0) || !(y0 == y0) || !(x1 == x1) ||
+             !(y1 == y1))
                 ? 1
                 : 0;
   i0 = i0 < 0 ? 0 : (i0 > L.nx - 1 ? L.nx - 1 : i0);
   i1 = i1 < 0 ? 0 : (i1 > L.nx - 1 ? L.nx - 1 : i1);
   j0 = j0 < 0 ? 0 : (j0 > L.ny - 1 ? L.ny - 1 : j0);
   j1 = j1 < 0 ? 0 : (j1 > L.ny - 1 ? L.ny - 1 : j1);
-  g.ti0 = i0 / kTileX;
-  g.ti1 = i1 / kTileX;
+  g.ti0 = i0 / tile_w;
+  g.ti1 = i1 / tile_w;
   g.tj0 = j0 / kTileY;
   g.tj1 = j1 / kTileY;
   if (g.ti1 > ntiles_x - 1) g.ti1 = ntiles_x - 1;
@@ -382,8 +491,19 @@ __host__ __device__ inline ForceRegion make_region(const Lattice &L, double xg, 
   return g;
 }
 
+// the same for a disk of radius r centred at (xg, yg)
+__host__ __device__ inline ForceRegion make_region(const Lattice &L, double xg, double yg,
+                                                   double r, int ntiles_x, int ntiles_y,
+                                                   int tile_w) {
+  return make_region_box(L, xg - r, xg + r, yg - r, yg + r, ntiles_x, ntiles_y, tile_w);
+}
+
 // launches (step.cu)
-cudaError_t launch_step(int dtype, bool gather, const StepArgs &a, cudaStream_t s);
+// the special kernel: SIM blocks, edge nodes, force-region tiles and the
+// FP64 tail (or every tile, with all_tiles set)
+cudaError_t launch_special(int dtype, bool gather, const StepArgs &a, cudaStream_t s);
+// the bulk kernel: the nodes off the edges, outside the force-region tiles
+cudaError_t launch_bulk(int dtype, const StepArgs &a, cudaStream_t s);
 
 // auxiliary kernels (aux.cu)
 cudaError_t launch_raster(const Lattice &L, const BodyState *body, uint8_t *chi, int i0, int j0,
