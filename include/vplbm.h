@@ -46,10 +46,12 @@ typedef enum {
                           SIM point without a fluid node) */
 } vplbm_status;
 
-/* Storage of the populations.  All forms store the offsets h_a = f_a - w_a
- * (w_a the lattice weights).  F64 computes in FP64; F32, F16_OFS and BF16_OFS
- * compute the step in FP32 (the 16-bit forms round to nearest even on store).
- * Force reductions and the rigid-body update are FP64 in every form. */
+/* Storage of the populations.  All forms store offsets h_a = f_a - E_a from
+ * E_a = feq_a(1, u_ref) (config.u_ref; zero gives the lattice weights w_a).
+ * F64 computes in FP64; F32, F16_OFS and BF16_OFS compute the step in FP32
+ * (the 16-bit forms round to nearest even on store).  Force sums are exact
+ * 64-bit fixed-point integers converted to FP64; the rigid-body update is
+ * FP64 in every form. */
 typedef enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFS = 2, VPLBM_BF16_OFS = 3 } vplbm_dtype;
 
 /* Collision operator: BGK (Sec. 2.2) or TRT (Eq. TRT) with
@@ -93,6 +95,11 @@ typedef struct {
   double eta;              /* penalization factor, > 0 (1e-6 in Sec. 3) */
   double u_in[2];          /* inlet velocity and the initial fluid velocity */
   double body_force[2];    /* uniform force density on every node (0 in the paper) */
+  double u_ref[2];         /* populations are stored as f_a - feq_a(1, u_ref): (0, 0)
+                              stores the offsets from the lattice weights; the
+                              free-stream velocity keeps undisturbed regions near
+                              zero (smaller rounding in FP32 / 16-bit storage);
+                              |u_ref| < 0.3 */
 } vplbm_config;
 
 typedef struct {

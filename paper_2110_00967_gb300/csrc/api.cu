@@ -104,7 +104,9 @@ const char *check_config(const vplbm_config *c) {
   if (!(c->eta > 0.0)) return "eta must be > 0";
   if (c->sim_every < 0 || c->max_sim_points < 0 || c->history_len < 0) return "negative count";
   for (int k = 0; k < 2; ++k)
-    if (!std::isfinite(c->u_in[k]) || !std::isfinite(c->body_force[k])) return "non-finite velocity or force";
+    if (!std::isfinite(c->u_in[k]) || !std::isfinite(c->body_force[k]) || !std::isfinite(c->u_ref[k]))
+      return "non-finite velocity or force";
+  if (c->u_ref[0] * c->u_ref[0] + c->u_ref[1] * c->u_ref[1] > 0.09) return "|u_ref| must be below 0.3";
   const int x0 = c->bc[0], x1 = c->bc[1], y0 = c->bc[2], y1 = c->bc[3];
   auto xok = [](int b) {
     return b == VPLBM_PERIODIC || b == VPLBM_INLET_BB || b == VPLBM_OUTLET_CONVECTIVE || b == VPLBM_NOSLIP_BB;
@@ -432,12 +434,30 @@ vplbm_status vplbm_create(const vplbm_config *cfg, void *dev_workspace, size_t b
   L.pitch = pitch_of(cfg->nx);
   L.plane = plane_of(*cfg);
   for (int k = 0; k < 4; ++k) L.bc[k] = cfg->bc[k];
+  // offsets from E_a = feq_a(1, u_ref) and the side-condition constants on
+  // them: E_abar - E_a = -6 w_a c_a.u_ref (the odd part of the equilibrium),
+  // plus the moving-wall term 2 w_a rho_w (c_a.u_in) / cs2 (rho_w = 1) at the
+  // inlet; a symmetry wall flips c_y
+  // FP32 paths carry u_ref in FP32: the offsets are defined from exactly that
+  // value so that the kernels and the conversions agree on E to the last bit
+  const bool f64 = cfg->dtype == VPLBM_F64;
+  L.ur[0] = f64 ? cfg->u_ref[0] : (double)(float)cfg->u_ref[0];
+  L.ur[1] = f64 ? cfg->u_ref[1] : (double)(float)cfg->u_ref[1];
   for (int a = 0; a < 9; ++a) {
-    // inlet bounce-back from a wall moving at u_in: 2 w_a rho_w (c_a.u_in) / cs2, rho_w = 1
-    const double cu = cx_of(a) * cfg->u_in[0] + cy_of(a) * cfg->u_in[1];
-    L.kin[a] = 2.0 * w_of(a) * cu * 3.0;
+    const double cr = cx_of(a) * L.ur[0] + cy_of(a) * L.ur[1];
+    const double uu = L.ur[0] * L.ur[0] + L.ur[1] * L.ur[1];
+    L.E[a] = w_of(a) * (1.0 + 3.0 * cr + 4.5 * cr * cr - 1.5 * uu);
+    const double cin = cx_of(a) * (cfg->u_in[0] - L.ur[0]) + cy_of(a) * (cfg->u_in[1] - L.ur[1]);
+    L.kin[a] = 6.0 * w_of(a) * cin;
+    L.knos[a] = -6.0 * w_of(a) * cr;
+    L.ksym[a] = w_of(a) * (-6.0 * cy_of(a) * L.ur[1] - 18.0 * cx_of(a) * cy_of(a) * L.ur[0] * L.ur[1]);
+    L.E_f[a] = (float)L.E[a];
     L.kin_f[a] = (float)L.kin[a];
+    L.knos_f[a] = (float)L.knos[a];
+    L.ksym_f[a] = (float)L.ksym[a];
   }
+  L.ur_f[0] = (float)L.ur[0];
+  L.ur_f[1] = (float)L.ur[1];
   L.uc = sqrt(cfg->u_in[0] * cfg->u_in[0] + cfg->u_in[1] * cfg->u_in[1]);
   L.bf[0] = cfg->body_force[0];
   L.bf[1] = cfg->body_force[1];

@@ -37,7 +37,7 @@ __global__ void interface_kernel(Lattice L, uint8_t *chi, int i0, int j0, int w,
 }
 
 // f = feq(1, u0) with u0 = u_in on fluid nodes and the rigid velocity on
-// solid nodes; stored as offsets f - w
+// solid nodes; stored as offsets f - E
 template <typename S>
 __global__ void init_kernel(Lattice L, const BodyState *body, const uint8_t *chi, S *buf,
                             double u0x, double u0y) {
@@ -51,11 +51,15 @@ __global__ void init_kernel(Lattice L, const BodyState *body, const uint8_t *chi
     ux = b.ux - b.omega * ((double)j - b.yg);
     uy = b.uy + b.omega * ((double)i - b.xg);
   }
-  const double uu = ux * ux + uy * uy;
+  // feq(1, u0) - E = w (Q(u0) - Q(u_ref)) with Q(u) = 3 c.u + 4.5 (c.u)^2 - 1.5 |u|^2,
+  // written with du = u0 - u_ref
+  const double dux = ux - L.ur[0], duy = uy - L.ur[1];
+  const double dsu = dux * (ux + L.ur[0]) + duy * (uy + L.ur[1]);
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    const double cu = cx_of(a) * ux + cy_of(a) * uy;
-    const double h = w_of(a) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);  // feq(1,u) - w
+    const double cdu = cx_of(a) * dux + cy_of(a) * duy;
+    const double csu = cx_of(a) * (ux + L.ur[0]) + cy_of(a) * (uy + L.ur[1]);
+    const double h = w_of(a) * (3.0 * cdu + 4.5 * cdu * csu - 1.5 * dsu);
     buf[(int64_t)a * L.plane + node] = Store<S>::from_double(h);
   }
 }
@@ -69,7 +73,7 @@ __global__ void get_f_kernel(Lattice L, const S *buf, const typename Store<S>::T
   const int i = (int)(k % L.nx), j = (int)(k / L.nx);
 #pragma unroll
   for (int a = 0; a < 9; ++a)
-    out[a * n + k] = (double)pre_pop<S, kGather>(buf, prev, L, a, i, j) + w_of(a);
+    out[a * n + k] = (double)pre_pop<S, kGather>(buf, prev, L, a, i, j) + L.E[a];
 }
 
 // macroscopic fields of Eqs. updatestep and updatestepm, FP64
@@ -85,7 +89,7 @@ __global__ void get_fields_kernel(Lattice L, const S *buf, const typename Store<
   double rho = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    const double f = (double)pre_pop<S, kGather>(buf, prev, L, a, i, j) + w_of(a);
+    const double f = (double)pre_pop<S, kGather>(buf, prev, L, a, i, j) + L.E[a];
     rho += f;
     jx += cx_of(a) * f;
     jy += cy_of(a) * f;
@@ -114,7 +118,7 @@ __global__ void set_state_kernel(Lattice L, const double *f, S *buf) {
   const int64_t node = (int64_t)j * L.pitch + i;
 #pragma unroll
   for (int a = 0; a < 9; ++a)
-    buf[(int64_t)a * L.plane + node] = Store<S>::from_double(f[a * n + k] - w_of(a));
+    buf[(int64_t)a * L.plane + node] = Store<S>::from_double(f[a * n + k] - L.E[a]);
 }
 
 // outlet column (a = 3, 6, 7 at i = nx - 1) of a pre-collision FP64 field,
@@ -125,9 +129,9 @@ __global__ void set_prev_kernel(Lattice L, const double *f, T *prev) {
   if (j >= L.ny) return;
   const int64_t n = (int64_t)L.nx * L.ny;
   const int64_t k = (int64_t)j * L.nx + (L.nx - 1);
-  prev[0 * L.ny + j] = (T)(f[3 * n + k] - w_of(3));
-  prev[1 * L.ny + j] = (T)(f[6 * n + k] - w_of(6));
-  prev[2 * L.ny + j] = (T)(f[7 * n + k] - w_of(7));
+  prev[0 * L.ny + j] = (T)(f[3 * n + k] - L.E[3]);
+  prev[1 * L.ny + j] = (T)(f[6 * n + k] - L.E[6]);
+  prev[2 * L.ny + j] = (T)(f[7 * n + k] - L.E[7]);
 }
 
 __global__ void get_mask_kernel(Lattice L, const uint8_t *chi, uint8_t *out) {

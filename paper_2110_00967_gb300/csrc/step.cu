@@ -78,11 +78,12 @@ __device__ __forceinline__ void warp_add(const FixAcc<T> &a, unsigned long long 
 
 // The part of the stress beyond -(1/3) I at a fluid node,
 // sigma + (1/3) I = -(rho - 1)/3 I - (1 - 1/(2 tau+)) sum c c (f - feq),
-// from its pre-collision offsets, in the compute type (all terms are small).
+// from its pre-collision offsets, in the compute type (all terms are small;
+// f - feq = h - heq, with heq the equilibrium's offset as in collide()).
 template <typename S, bool kGather>
 __device__ __forceinline__ void node_stress(const S *buf, const typename Store<S>::T *prev,
-                                            const Lattice &L, typename Store<S>::T s, int i,
-                                            int j, typename Store<S>::T sig[3]) {
+                                            const Lattice &L, const Consts<typename Store<S>::T> &c,
+                                            int i, int j, typename Store<S>::T sig[3]) {
   using T = typename Store<S>::T;
   T h[9];
 #pragma unroll
@@ -95,22 +96,27 @@ __device__ __forceinline__ void node_stress(const S *buf, const typename Store<S
     jy += (T)cy_of(a) * h[a];
   }
   const T rho = (T)1 + drho;
-  jx += (T)0.5 * lat_bf<T>(L, 0);
-  jy += (T)0.5 * lat_bf<T>(L, 1);
-  const T ux = jx / rho, uy = jy / rho, uu = ux * ux + uy * uy;
+  const T inv = (T)1 / rho;
+  const T dux = (jx + (T)0.5 * lat_bf<T>(L, 0) - drho * c.urx) * inv;
+  const T duy = (jy + (T)0.5 * lat_bf<T>(L, 1) - drho * c.ury) * inv;
+  const T ux = c.urx + dux, uy = c.ury + duy, uu = ux * ux + uy * uy;
+  const T dsu = dux * (ux + c.urx) + duy * (uy + c.ury);
   T pxx = 0, pxy = 0, pyy = 0;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const T cu = (T)cx_of(a) * ux + (T)cy_of(a) * uy;
-    const T heq = (T)w_of(a) * (drho + rho * ((T)3 * cu + (T)4.5 * cu * cu - (T)1.5 * uu));
+    const T cdu = (T)cx_of(a) * dux + (T)cy_of(a) * duy;
+    const T csu = cu + ((T)cx_of(a) * c.urx + (T)cy_of(a) * c.ury);
+    const T heq = (T)w_of(a) * (drho * ((T)1 + (T)3 * cu + (T)4.5 * cu * cu - (T)1.5 * uu) +
+                                (T)3 * cdu + (T)4.5 * cdu * csu - (T)1.5 * dsu);
     const T d = h[a] - heq;
     pxx += (T)(cx_of(a) * cx_of(a)) * d;
     pxy += (T)(cx_of(a) * cy_of(a)) * d;
     pyy += (T)(cy_of(a) * cy_of(a)) * d;
   }
-  sig[0] = -drho / (T)3 - s * pxx;
-  sig[1] = -s * pxy;
-  sig[2] = -drho / (T)3 - s * pyy;
+  sig[0] = -drho / (T)3 - c.sim_s * pxx;
+  sig[1] = -c.sim_s * pxy;
+  sig[2] = -drho / (T)3 - c.sim_s * pyy;
 }
 
 // first fluid node of q_k = (qi, qj) + k c_a, k = 0..3, inside the lattice
@@ -176,7 +182,7 @@ __device__ __noinline__ FixAcc<typename Store<S>::T> sim_point(const StepArgs &p
       }
       if (first < 0) first = qj * p.L.nx + qi;
       T s3[3];
-      node_stress<S, kGather>(buf, prev, p.L, Consts<T>(p).sim_s, qi, qj, s3);
+      node_stress<S, kGather>(buf, prev, p.L, Consts<T>(p), qi, qj, s3);
       sig[0] += s3[0];
       sig[1] += s3[1];
       sig[2] += s3[2];
@@ -206,7 +212,7 @@ __device__ __noinline__ FixAcc<typename Store<S>::T> sim_point(const StepArgs &p
 // neighbour of the other phase, the fluid end adds (c_a - u_Gamma) f~_a and
 // the solid end subtracts its own (c_a - u_Gamma) f~_a, with x_Gamma the link
 // midpoint and u_Gamma the rigid velocity there; torques about the reference
-// point (Eq. fluidtorque).  f~ = h~ + w is split so that the w parts, which
+// point (Eq. fluidtorque).  f~ = h~ + E is split so that the E parts, which
 // cancel in pairs around a fixed body, are rounded exactly.
 template <typename T>
 __device__ __forceinline__ void mem_terms(const StepArgs &p, const T (&o)[9], int i, int j,
@@ -225,7 +231,7 @@ __device__ __forceinline__ void mem_terms(const StepArgs &p, const T (&o)[9], in
     const T ry = ((T)j - b.yg) + (T)(0.5 * cy_of(a));
     const T vx = (T)cx_of(a) - (b.ux - b.om * ry);
     const T vy = (T)cy_of(a) - (b.uy + b.om * rx);
-    const T ah = sg * o[a], aw = sg * (T)w_of(a);
+    const T ah = sg * o[a], aw = sg * LatC<T>::E(L, a);
     const T lxh = vx * ah, lyh = vy * ah, lxw = vx * aw, lyw = vy * aw;
     acc.add(0, lxh);
     acc.add(0, lxw);
@@ -358,17 +364,23 @@ __device__ void tail(const StepArgs &p, const ForceRegion &reg) {
 // node update
 // ---------------------------------------------------------------------------
 
-// BGK/TRT collision with the forcing term (Eq. TRT) of one node from its
-// moments, into o.  kForce = false drops the forcing term (G = 0: a fluid
-// node without body force).
+// BGK/TRT collision with the forcing term (Eq. TRT) of one node, into o.
+// The equilibrium enters through its offset heq = feq(rho, u) - E, written
+// with the small quantities drho = rho - 1 and du = u - u_ref only:
+// heq_a = w_a [drho (1 + Q_a(u)) + Q_a(u) - Q_a(u_ref)],
+// Q_a(u) = 3 c.u + 4.5 (c.u)^2 - 1.5 |u|^2, split into its even and odd parts
+// for TRT.  kForce = false drops the forcing term (G = 0: a fluid node
+// without body force).
 template <typename T, bool kForce>
-__device__ __forceinline__ void collide(const T (&h)[9], T drho, T rho, T ux, T uy, T gx, T gy,
+__device__ __forceinline__ void collide(const T (&h)[9], T drho, T dux, T duy, T gx, T gy,
                                         const Consts<T> &c, T (&o)[9]) {
+  const T ux = c.urx + dux, uy = c.ury + duy;
   const T uu = ux * ux + uy * uy;
+  const T dsu = dux * (ux + c.urx) + duy * (uy + c.ury);  // |u|^2 - |u_ref|^2
   const T ug = kForce ? ux * gx + uy * gy : (T)0;
   {
     const T w0 = (T)w_of(0);
-    const T heq0 = w0 * (drho - (T)1.5 * rho * uu);
+    const T heq0 = w0 * (drho * ((T)1 - (T)1.5 * uu) - (T)1.5 * dsu);
     T r = h[0] - c.s_plus * (h[0] - heq0);
     if (kForce) r += c.a_plus * (w0 * ((T)-3 * ug));
     o[0] = r;
@@ -379,8 +391,11 @@ __device__ __forceinline__ void collide(const T (&h)[9], T drho, T rho, T ux, T 
     const int b = opp_of(a);
     const T w = (T)w_of(a);
     const T cu = (T)cx_of(a) * ux + (T)cy_of(a) * uy;
-    const T heqp = w * (drho + rho * ((T)4.5 * cu * cu - (T)1.5 * uu));
-    const T heqm = w * (T)3 * rho * cu;
+    const T cdu = (T)cx_of(a) * dux + (T)cy_of(a) * duy;
+    const T csu = cu + ((T)cx_of(a) * c.urx + (T)cy_of(a) * c.ury);
+    const T heqp = w * (drho * ((T)1 + (T)4.5 * cu * cu - (T)1.5 * uu) + (T)4.5 * cdu * csu -
+                        (T)1.5 * dsu);
+    const T heqm = w * (T)3 * (drho * cu + cdu);
     const T hp = (T)0.5 * (h[a] + h[b]);
     const T hm = (T)0.5 * (h[a] - h[b]);
     T dp = -c.s_plus * (hp - heqp);
@@ -405,32 +420,36 @@ __device__ __forceinline__ bool update_node(const T (&h)[9], uint8_t m, int i, i
                                             const Consts<T> &cst, T (&o)[9]) {
   const T drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
   const T rho = (T)1 + drho;
-  T jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
-  T jy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
+  // j - u_ref (the offsets' first moment; sum_a c_a E_a = u_ref)
+  T djx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+  T djy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
   if ((m & kSolid) || L.has_bf) {
     const T bfx = lat_bf<T>(L, 0), bfy = lat_bf<T>(L, 1);
-    jx += (T)0.5 * bfx;
-    jy += (T)0.5 * bfy;
-    T ux, uy, gx = bfx, gy = bfy;
+    djx += (T)0.5 * bfx;
+    djy += (T)0.5 * bfy;
+    T dux, duy, gx = bfx, gy = bfy;
     if (m & kSolid) {
       T usx, usy;
       solid_velocity<T>(*body, i, j, usx, usy);
       const T k = cst.half_pen;
       const T den = rho + k * rho;
-      ux = (jx + k * rho * usx) / den;
-      uy = (jy + k * rho * usy) / den;
+      // u - u_ref = (j + k rho u_s)/(rho (1 + k)) - u_ref
+      dux = (djx - drho * cst.urx + k * rho * (usx - cst.urx)) / den;
+      duy = (djy - drho * cst.ury + k * rho * (usy - cst.ury)) / den;
+      // G = -(chi/eta)(j - rho u_s)/(1 + k)
       const T pen = (T)2 * k;
-      gx -= pen * (jx - rho * usx) / ((T)1 + k);
-      gy -= pen * (jy - rho * usy) / ((T)1 + k);
+      gx -= pen * (djx - drho * usx + (cst.urx - usx)) / ((T)1 + k);
+      gy -= pen * (djy - drho * usy + (cst.ury - usy)) / ((T)1 + k);
     } else {
       const T inv = (T)1 / rho;
-      ux = jx * inv;
-      uy = jy * inv;
+      dux = (djx - drho * cst.urx) * inv;
+      duy = (djy - drho * cst.ury) * inv;
     }
-    collide<T, true>(h, drho, rho, ux, uy, gx, gy, cst, o);
+    collide<T, true>(h, drho, dux, duy, gx, gy, cst, o);
   } else {
     const T inv = (T)1 / rho;
-    collide<T, false>(h, drho, rho, jx * inv, jy * inv, (T)0, (T)0, cst, o);
+    collide<T, false>(h, drho, (djx - drho * cst.urx) * inv, (djy - drho * cst.ury) * inv, (T)0,
+                      (T)0, cst, o);
   }
   return !(rho > (T)0) || !isfinite(rho);
 }
@@ -586,18 +605,19 @@ __global__ void __launch_bounds__(kThreads) bulk_kernel(const StepArgs p) {
   const Consts<T> cst(p);
   const T drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
   const T rho = (T)1 + drho;
-  T jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
-  T jy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
+  T djx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+  T djy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
   T o[9];
+  const T inv = (T)1 / rho;
   if (kForce) {
     const T bfx = lat_bf<T>(L, 0), bfy = lat_bf<T>(L, 1);
-    jx += (T)0.5 * bfx;
-    jy += (T)0.5 * bfy;
-    const T inv = (T)1 / rho;
-    collide<T, true>(h, drho, rho, jx * inv, jy * inv, bfx, bfy, cst, o);
+    djx += (T)0.5 * bfx;
+    djy += (T)0.5 * bfy;
+    collide<T, true>(h, drho, (djx - drho * cst.urx) * inv, (djy - drho * cst.ury) * inv, bfx,
+                     bfy, cst, o);
   } else {
-    const T inv = (T)1 / rho;
-    collide<T, false>(h, drho, rho, jx * inv, jy * inv, (T)0, (T)0, cst, o);
+    collide<T, false>(h, drho, (djx - drho * cst.urx) * inv, (djy - drho * cst.ury) * inv, (T)0,
+                      (T)0, cst, o);
   }
 #pragma unroll
   for (int a = 0; a < 9; ++a) Store<S>::st(dst + (int64_t)a * L.plane + node, o[a]);

@@ -215,14 +215,26 @@ constexpr int kAccWords = 2 * kAccSlots;
 // ---------------------------------------------------------------------------
 // lattice geometry and side conditions, shared by every kernel
 // ---------------------------------------------------------------------------
+// Populations are stored as offsets h_a = f_a - E_a from the equilibrium at
+// rest density and a reference velocity, E_a = feq_a(1, u_ref): with
+// u_ref = 0 these are the offsets from the lattice weights; with u_ref the
+// free-stream velocity the stored values are small wherever the flow is
+// undisturbed, which keeps rounding small in the reduced-precision forms.
+// Every formula below works on these offsets and on small differences
+// (rho - 1, u - u_ref) only.
 struct Lattice {
   int32_t nx, ny, pitch;
   int32_t bc[4];
-  int64_t plane;     // ny * pitch
-  double kin[9];     // inlet bounce-back terms 2 w_a (c_a.u_in)/cs2
+  int64_t plane;     // ny * pitch (+ padding)
+  double E[9];       // feq_a(1, u_ref)
+  double ur[2];      // u_ref
+  // side-condition constants on the offsets: a population that returns by
+  // bounce-back from an inlet wall gets kin, from a no-slip wall knos, and one
+  // reflected on a symmetry wall gets ksym
+  double kin[9], knos[9], ksym[9];
   double uc;         // convective outlet velocity |u_in|
   double bf[2];      // uniform body force density
-  float kin_f[9];    // the same in FP32 (no FP64 work on FP32 paths)
+  float E_f[9], ur_f[2], kin_f[9], knos_f[9], ksym_f[9];  // FP32 copies
   float uc_f;
   float bf_f[2];
   int32_t has_bf;    // body force nonzero: every node carries a forcing term
@@ -230,23 +242,29 @@ struct Lattice {
 
 // lattice constants in the compute type
 template <typename T>
-__device__ __forceinline__ T lat_kin(const Lattice &L, int a);
+struct LatC;
 template <>
-__device__ __forceinline__ double lat_kin<double>(const Lattice &L, int a) { return L.kin[a]; }
+struct LatC<double> {
+  static __device__ __forceinline__ double kin(const Lattice &L, int a) { return L.kin[a]; }
+  static __device__ __forceinline__ double knos(const Lattice &L, int a) { return L.knos[a]; }
+  static __device__ __forceinline__ double ksym(const Lattice &L, int a) { return L.ksym[a]; }
+  static __device__ __forceinline__ double E(const Lattice &L, int a) { return L.E[a]; }
+  static __device__ __forceinline__ double ur(const Lattice &L, int k) { return L.ur[k]; }
+  static __device__ __forceinline__ double uc(const Lattice &L) { return L.uc; }
+  static __device__ __forceinline__ double bf(const Lattice &L, int k) { return L.bf[k]; }
+};
 template <>
-__device__ __forceinline__ float lat_kin<float>(const Lattice &L, int a) { return L.kin_f[a]; }
+struct LatC<float> {
+  static __device__ __forceinline__ float kin(const Lattice &L, int a) { return L.kin_f[a]; }
+  static __device__ __forceinline__ float knos(const Lattice &L, int a) { return L.knos_f[a]; }
+  static __device__ __forceinline__ float ksym(const Lattice &L, int a) { return L.ksym_f[a]; }
+  static __device__ __forceinline__ float E(const Lattice &L, int a) { return L.E_f[a]; }
+  static __device__ __forceinline__ float ur(const Lattice &L, int k) { return L.ur_f[k]; }
+  static __device__ __forceinline__ float uc(const Lattice &L) { return L.uc_f; }
+  static __device__ __forceinline__ float bf(const Lattice &L, int k) { return L.bf_f[k]; }
+};
 template <typename T>
-__device__ __forceinline__ T lat_uc(const Lattice &L);
-template <>
-__device__ __forceinline__ double lat_uc<double>(const Lattice &L) { return L.uc; }
-template <>
-__device__ __forceinline__ float lat_uc<float>(const Lattice &L) { return L.uc_f; }
-template <typename T>
-__device__ __forceinline__ T lat_bf(const Lattice &L, int k);
-template <>
-__device__ __forceinline__ double lat_bf<double>(const Lattice &L, int k) { return L.bf[k]; }
-template <>
-__device__ __forceinline__ float lat_bf<float>(const Lattice &L, int k) { return L.bf_f[k]; }
+__device__ __forceinline__ T lat_bf(const Lattice &L, int k) { return LatC<T>::bf(L, k); }
 
 // Pull-form streaming: the pre-collision population a at node (i, j) of the
 // time level whose post-collision field is `post` (previous level) and whose
@@ -274,12 +292,12 @@ __device__ __forceinline__ typename Store<S>::T gather_core(const S *post, const
   if (xin && yin) return pop_at(post, L, a, si, sj);
   if (!xin) {
     const int kind = L.bc[si < 0 ? 0 : 1];
-    if (kind == VPLBM_INLET_BB) return pop_at(post, L, opp_of(a), i, j) + lat_kin<T>(L, a);
-    return pop_at(post, L, opp_of(a), i, j);  // no-slip bounce-back
+    if (kind == VPLBM_INLET_BB) return pop_at(post, L, opp_of(a), i, j) + LatC<T>::kin(L, a);
+    return pop_at(post, L, opp_of(a), i, j) + LatC<T>::knos(L, a);  // no-slip bounce-back
   }
   const int kind = L.bc[sj < 0 ? 2 : 3];
-  if (kind == VPLBM_SYMMETRY) return pop_at(post, L, flipy_of(a), si, j);
-  return pop_at(post, L, opp_of(a), i, j);  // no-slip bounce-back
+  if (kind == VPLBM_SYMMETRY) return pop_at(post, L, flipy_of(a), si, j) + LatC<T>::ksym(L, a);
+  return pop_at(post, L, opp_of(a), i, j) + LatC<T>::knos(L, a);  // no-slip bounce-back
 }
 
 __device__ __forceinline__ int outlet_slot(int a) { return a == 3 ? 0 : (a == 6 ? 1 : 2); }
@@ -295,7 +313,7 @@ __device__ __forceinline__ typename Store<S>::T gather(const S *post,
     // convective outlet: f^{n+1}(N-1) = (f^n(N-1) + U_c f^{n+1}(N-2)) / (1 + U_c)
     const T inner = gather_core(post, L, a, i - 1, j);
     const T old = prev[outlet_slot(a) * L.ny + j];
-    const T uc = lat_uc<T>(L);
+    const T uc = LatC<T>::uc(L);
     return (old + uc * inner) / ((T)1 + uc);
   }
   return gather_core(post, L, a, i, j);
@@ -450,17 +468,17 @@ template <typename T>
 struct Consts;
 template <>
 struct Consts<double> {
-  double s_plus, s_minus, a_plus, a_minus, half_pen, sim_s;
+  double s_plus, s_minus, a_plus, a_minus, half_pen, sim_s, urx, ury;
   __device__ __forceinline__ explicit Consts(const StepArgs &p)
       : s_plus(p.s_plus), s_minus(p.s_minus), a_plus(p.a_plus), a_minus(p.a_minus),
-        half_pen(p.half_pen), sim_s(1.0 - 0.5 / p.tau_plus) {}
+        half_pen(p.half_pen), sim_s(1.0 - 0.5 / p.tau_plus), urx(p.L.ur[0]), ury(p.L.ur[1]) {}
 };
 template <>
 struct Consts<float> {
-  float s_plus, s_minus, a_plus, a_minus, half_pen, sim_s;
+  float s_plus, s_minus, a_plus, a_minus, half_pen, sim_s, urx, ury;
   __device__ __forceinline__ explicit Consts(const StepArgs &p)
       : s_plus(p.f_s_plus), s_minus(p.f_s_minus), a_plus(p.f_a_plus), a_minus(p.f_a_minus),
-        half_pen(p.f_half_pen), sim_s(p.f_sim_s) {}
+        half_pen(p.f_half_pen), sim_s(p.f_sim_s), urx(p.L.ur_f[0]), ury(p.L.ur_f[1]) {}
 };
 
 // tile range of the force region of a body whose bounding box is

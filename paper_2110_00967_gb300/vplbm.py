@@ -39,7 +39,7 @@ class vplbm_config(C.Structure):
         ("forcing", C.c_int32), ("bc", C.c_int32 * 4), ("sim_every", C.c_int32),
         ("max_sim_points", C.c_int32), ("history_len", C.c_int32),
         ("tau_plus", C.c_double), ("lambda_trt", C.c_double), ("eta", C.c_double),
-        ("u_in", C.c_double * 2), ("body_force", C.c_double * 2),
+        ("u_in", C.c_double * 2), ("body_force", C.c_double * 2), ("u_ref", C.c_double * 2),
     ]
 
 
@@ -56,7 +56,7 @@ class vplbm_body(C.Structure):
 def config(nx, ny, dtype=F32, collision=TRT, forcing=FORCING_PAPER,
            bc=(PERIODIC, PERIODIC, PERIODIC, PERIODIC), sim_every=1, max_sim_points=0,
            history_len=0, tau_plus=0.8, lambda_trt=1.0 / 6.0, eta=1e-6, u_in=(0.0, 0.0),
-           body_force=(0.0, 0.0)) -> vplbm_config:
+           body_force=(0.0, 0.0), u_ref=(0.0, 0.0)) -> vplbm_config:
     c = vplbm_config()
     c.nx, c.ny, c.dtype, c.collision, c.forcing = nx, ny, dtype, collision, forcing
     for k in range(4):
@@ -65,6 +65,7 @@ def config(nx, ny, dtype=F32, collision=TRT, forcing=FORCING_PAPER,
     c.tau_plus, c.lambda_trt, c.eta = tau_plus, lambda_trt, eta
     c.u_in[0], c.u_in[1] = u_in
     c.body_force[0], c.body_force[1] = body_force
+    c.u_ref[0], c.u_ref[1] = u_ref
     return c
 
 
@@ -383,7 +384,8 @@ def config_of(w, dtype: str | None = None, **over) -> vplbm_config:
               collision=BGK if w.collision == "bgk" else TRT,
               forcing=FORCING_PAPER if w.forcing == "paper" else FORCING_SPLIT,
               bc=tuple(_BCS[b] for b in w.bc), sim_every=w.sim_every, tau_plus=w.tau_plus,
-              lambda_trt=w.lambda_trt, eta=w.eta, u_in=w.u_in, body_force=w.body_force)
+              lambda_trt=w.lambda_trt, eta=w.eta, u_in=w.u_in, body_force=w.body_force,
+              u_ref=w.u_ref)
     kw.update(over)
     return config(**kw)
 

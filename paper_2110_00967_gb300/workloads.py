@@ -59,6 +59,7 @@ class Workload:
     forcing: str = "paper"
     body_force: tuple = (0.0, 0.0)
     sim_every: int = 1
+    u_ref: tuple = (0.0, 0.0)  # stored offsets f - feq(1, u_ref); (0, 0): f - w
 
     @property
     def reference_length(self) -> float:
@@ -78,20 +79,24 @@ def disk_channel() -> Workload:
 
 
 def naca(alpha_deg: float = 0.0, dtype: str = "f32", nx: int = 2048, ny: int = 1024,
-         chord: float | None = None, steps: int = 200_000) -> Workload:
+         chord: float | None = None, steps: int = 200_000, u_ref=None) -> Workload:
     """NACA 0012 at Re 1000 on the chord (C = 200 on 2048 x 1024): leading edge
     at x = 4C, chord line half-way between the two middle rows, rotation about
     the quarter chord (nose up for alpha > 0), inlet u = 0.05, convective
     outlet, symmetry top and bottom, TRT with Lambda = 1/6 (Sec. 2.2, 3.1).
-    Smaller grids scale the geometry with nx (C = nx * 200 / 2048)."""
+    Smaller grids scale the geometry with nx (C = nx * 200 / 2048).
+    Reduced-precision forms store offsets from the free-stream equilibrium
+    (u_ref = u_in) unless u_ref is given; (0, 0) gives the f - w offsets."""
     c = chord if chord is not None else nx * 200.0 / 2048.0
+    if u_ref is None:
+        u_ref = (0.0, 0.0) if dtype == "f64" else (0.05, 0.0)
     return Workload(
         name=f"naca0012-{nx}x{ny}-a{alpha_deg:g}-{dtype}", nx=nx, ny=ny, dtype=dtype,
         collision="trt", tau_plus=0.53,
         u_in=(0.05, 0.0), bc=(INLET, OUTLET, SYMMETRY, SYMMETRY),
         body=Body("naca", length=c, thickness=0.12, x_c=4.0 * c + 0.25 * c,
                   y_c=(ny - 1) / 2.0, angle_deg=alpha_deg),
-        steps=steps)
+        steps=steps, u_ref=tuple(u_ref))
 
 
 NACA_ANGLES = (0.0, 5.0, 10.0, 15.0, 20.0)
