@@ -222,6 +222,35 @@ vplbm_status vplbm_check(vplbm_ctx *ctx);
 /* Number of kernels the library has launched on this lattice so far. */
 vplbm_status vplbm_launch_count(vplbm_ctx *ctx, int64_t *n);
 
+/* The SIM force (F[0], F[1], T about ref) of a state the caller supplies,
+ * computed without any device allocation by the caller or the library.  For
+ * callers that cannot allocate device memory: code embedded in a host
+ * application whose allocator has already claimed the device memory, or
+ * latency-bound callers that cannot afford the device-wide synchronisation
+ * that cudaMalloc and cudaFree imply.  No counterpart in the paper: it
+ * evaluates the same SIM sum as vplbm_step (nearest node, or both nodes of an
+ * exact tie, walk along the lattice direction closest to the normal to the
+ * first fluid node, stress averaged over the candidates, summed in point
+ * order in FP64) on the inputs given here.
+ *   cfg     nx, ny, tau_plus and body_force are used;
+ *   f_dev   device, FP64 pre-collision populations [9][ny][nx];
+ *   chi_dev device, mask [ny][nx] (0 fluid, nonzero solid);
+ *   pts     host, n_pts rows (x - ref_x, y - ref_y, n_x, n_y, S);
+ *   ref     host, the reference point; out host, (F_x, F_y, T).
+ * The scratch is one fixed device array in the library of
+ * 8 * (8 + 4096) doubles (256 KiB), held by every GPU that loads the library
+ * until the process exits: n_pts above 4096 is rejected with EINVAL.  The
+ * first call on a device takes that array's device address with the device
+ * current; make that first call before any stream capture.  Every call uses
+ * the same array and leaves its contents behind (the call clears what must
+ * start at zero), so calls whose GPU work overlaps -- on two streams or from
+ * two threads -- race.  Synchronises cuda_stream; ESTATE when a point finds
+ * no fluid node (out then sums the other points); the text of a failure is
+ * vplbm_last_error(NULL). */
+vplbm_status vplbm_sim_force_static(const vplbm_config *cfg, const double *f_dev,
+                                    const uint8_t *chi_dev, int32_t n_pts, const double *pts,
+                                    const double ref[2], double out[3], void *cuda_stream);
+
 /* Releases the host-side context; never touches the caller's workspace.
  * NULL is accepted. */
 void vplbm_destroy(vplbm_ctx *ctx);

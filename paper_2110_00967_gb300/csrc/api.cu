@@ -238,6 +238,12 @@ struct vplbm_ctx {
 
 namespace {
 
+}  // namespace
+
+void vplbm::set_global_error(const std::string &msg) { g_err = msg; }
+
+namespace {
+
 vplbm_status fail(vplbm_ctx *c, vplbm_status st, const std::string &msg) {
   if (c)
     c->err = msg;

@@ -10,6 +10,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 #include "vplbm.h"
 
@@ -515,6 +516,9 @@ __host__ __device__ inline ForceRegion make_region(const Lattice &L, double xg, 
                                                    int tile_w) {
   return make_region_box(L, xg - r, xg + r, yg - r, yg + r, ntiles_x, ntiles_y, tile_w);
 }
+
+// failure text of calls without a context (api.cu), read by vplbm_last_error(NULL)
+void set_global_error(const std::string &msg);
 
 // launches (step.cu)
 // the special kernel: SIM blocks, edge nodes, force-region tiles and the

@@ -108,6 +108,8 @@ _SIGS = [
     ("vplbm_get_sim_nodes", [_vp, _P(C.c_int32), C.c_int32, _P(C.c_int32)], C.c_int),
     ("vplbm_check", [_vp], C.c_int),
     ("vplbm_launch_count", [_vp, _P(C.c_int64)], C.c_int),
+    ("vplbm_sim_force_static", [_P(vplbm_config), _vp, _vp, C.c_int32, _P(C.c_double),
+                                _P(C.c_double), _P(C.c_double), _vp], C.c_int),
     ("vplbm_destroy", [_vp], None),
     ("vplbm_last_error", [_vp], C.c_char_p),
 ]
@@ -253,6 +255,20 @@ def vplbm_launch_count(ctx) -> int:
     n = C.c_int64()
     _check(lib().vplbm_launch_count(ctx, C.byref(n)), ctx)
     return n.value
+
+
+def vplbm_sim_force_static(cfg: vplbm_config, f_dev_ptr: int, chi_dev_ptr: int, pts, ref,
+                           stream: int):
+    """SIM force of a supplied state with no device allocation (see
+    include/vplbm.h); pts is an (n, 5) float64 host array."""
+    pts = np.ascontiguousarray(pts, np.float64)
+    ref = np.ascontiguousarray(ref, np.float64)
+    out = np.zeros(3)
+    _check(lib().vplbm_sim_force_static(C.byref(cfg), f_dev_ptr, chi_dev_ptr, len(pts),
+                                        pts.ctypes.data_as(_P(C.c_double)),
+                                        ref.ctypes.data_as(_P(C.c_double)),
+                                        out.ctypes.data_as(_P(C.c_double)), stream))
+    return out
 
 
 def vplbm_destroy(ctx):
