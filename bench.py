@@ -7,7 +7,8 @@ benchmark step advances every lattice by one time step: the fused
 collide-penalize-stream kernel with the MEM force and the SIM force (849
 points) of that step.  Metric: million lattice-node updates per second
 (MLUPS) over all lattices and ranks.  The five lattices hold 5 x 151 MB of
-populations, more than the 129 MB L2, and are stepped in turn.
+populations, more than the 129 MB L2, and are stepped in turn as one batch
+(vplbm_batch_step: 32 steps of all five replayed from one CUDA graph).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -28,6 +29,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -39,6 +42,8 @@ KERNEL_SOURCES = ("paper_2110_00967_gb300/csrc/step.cu",
                   "paper_2110_00967_gb300/csrc/vplbm_internal.cuh",
                   "paper_2110_00967_gb300/csrc/api.cu")
 METRIC = "VP-LBM MLUPS"
+CHUNK = 32  # steps per graph replay of the batch
+HISTORY = 64  # force-history ring of each lattice
 WORKLOAD = "naca0012-re1000-2048x1024-f32-alpha0,5,10,15,20"
 
 
@@ -214,80 +219,65 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     works = [W.naca(a, dtype="f32") for a in ANGLES]
-    lats = [V.Lattice(V.config_of(w), device=dev) for w in works]
+    lats = [V.Lattice(V.config_of(w, history_len=HISTORY), device=dev) for w in works]
     for w, lat in zip(works, lats):
         lat.set_body(V.body_of(w))
-
-    def one_step():
-        for lat in lats:
-            lat.step(1)
-
-    for _ in range(args.warmup):
-        one_step()
+    # the five lattices advance in lockstep, 32-step runs replayed from one graph
+    batch = V.Batch(lats, stream=stream)
+    batch.step(args.warmup)
     torch.cuda.synchronize()
 
-    # device-timed region
-    n_ev = min(2000, args.steps * len(lats))
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(n_ev)]
+    # device-timed region: every lattice advances args.steps steps
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = sum(l.launches for l in lats)
+    l0 = batch.launches
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     barrier(world)
     torch.cuda.synchronize()
     if clocks:
         clocks.start()
         time.sleep(0.3)
-    k = 0
     start.record(stream)
-    for _ in range(args.steps):
-        for lat in lats:
-            if k < n_ev:
-                evs[k][0].record(stream)
-                lat.step(1)
-                evs[k][1].record(stream)
-            else:
-                lat.step(1)
-            k += 1
+    batch.step(args.steps)
     end.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
     barrier(world)
-    launches = sum(l.launches for l in lats) - l0
+    launches = batch.launches - l0
     elapsed_ms = reduce_max(start.elapsed_time(end), world, dev)
-    # per-launch device time; the first launches of the region are skipped
-    # while the launch queue fills
-    kern_ms = [a.elapsed_time(b) for a, b in evs][min(10, n_ev // 2):]
-    kern_avg_ms = sum(kern_ms) / len(kern_ms)
+    lattice_step_ms = elapsed_ms / (args.steps * len(lats))
     for lat in lats:
         lat.check()
 
-    # end-to-end through the public API: place the bodies (host geometry up),
-    # step, and read every step's forces back into pinned host memory
-    e2e_steps = max(50, min(args.steps, 2000))
-    pinned = torch.empty((e2e_steps, len(lats), 6), dtype=torch.float64, pin_memory=True)
-    lats2 = lats  # reuse the workspaces; set_body restarts each solve
+    # end-to-end through the public API with host buffers: place the bodies
+    # (geometry and body state up), step, and read every step's forces back
+    # (MEM and SIM, 32 steps at a time) into pinned host memory
+    e2e_steps = max(2 * CHUNK, min(args.steps, 2000) // CHUNK * CHUNK)
+    pinned = torch.empty((len(lats), e2e_steps, 2, CHUNK, 3), dtype=torch.float64,
+                         pin_memory=True).numpy()
     torch.cuda.synchronize()
+    barrier(world)
     t0 = time.perf_counter()
-    for w, lat in zip(works, lats2):
+    for w, lat in zip(works, lats):
         lat.set_body(V.body_of(w))
-    for s in range(e2e_steps):
-        for i, lat in enumerate(lats2):
-            lat.step(1)
-            V.vplbm_forces_async(lat.ctx, pinned[s, i].data_ptr())
+    for c in range(e2e_steps // CHUNK):
+        batch.step(CHUNK)
+        for i, lat in enumerate(lats):
+            pinned[i, c, 0] = lat.history(V.MEM, CHUNK)
+            pinned[i, c, 1] = lat.history(V.SIM, CHUNK)
     torch.cuda.synchronize()
     e2e_dt = reduce_max(time.perf_counter() - t0, world, dev)
-    assert bool(torch.isfinite(pinned[-1]).all())
+    assert np.isfinite(pinned[:, : e2e_steps // CHUNK]).all()
     body_bytes = 16 * 8 + 4 * 4  # device body state block
     sim_bytes = 849 * 48
     h2d = len(lats) * (body_bytes + sim_bytes) / e2e_steps
     d2h = len(lats) * 6 * 8
+    batch.close()
 
     nodes = NX * NY * len(lats)
     value = world * nodes * args.steps / (elapsed_ms / 1e3) / 1e6
     e2e_value = world * nodes * e2e_steps / e2e_dt / 1e6
     peak, peak_kind = measured_hbm_peak()
-    achieved = BYTES_PER_LUP * NX * NY / (kern_avg_ms / 1e3) / 1e9
+    achieved = BYTES_PER_LUP * NX * NY / (lattice_step_ms / 1e3) / 1e9
     traffic = profiled_traffic()
     if rank != 0:
         return None
@@ -299,8 +289,9 @@ def run_ours(args, rank, world, local_rank):
         "config": config_block({"parallelism": f"replicas{world}"}),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "one step: bulk_kernel<float> with special_kernel<float> beside it",
-                     "kernel_avg_us": round(kern_avg_ms * 1e3, 3),
+                     "kernel": "one lattice step: bulk_kernel<float> with special_kernel<float> "
+                               "beside it, timed over the region",
+                     "kernel_avg_us": round(lattice_step_ms * 1e3, 3),
                      "bytes_per_lup": BYTES_PER_LUP, "peak_kind": peak_kind},
         "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": d2h,

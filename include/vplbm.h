@@ -222,6 +222,39 @@ vplbm_status vplbm_check(vplbm_ctx *ctx);
 /* Number of kernels the library has launched on this lattice so far. */
 vplbm_status vplbm_launch_count(vplbm_ctx *ctx, int64_t *n);
 
+/* ---- batches: several lattices stepped together ----
+ * A batch steps n independent lattices (any sizes and storage types, one
+ * device) in lockstep on one stream: step k of lattice 0, of lattice 1, ...,
+ * of lattice n-1, then step k+1.  Each lattice ends in the state, with the
+ * force histories and sums, that stepping it alone would give (the lattices
+ * share no data).  Runs of 32 steps in which every lattice starts from an
+ * even time level since its last pre-collision state (vplbm_set_body or
+ * vplbm_set_state) and evaluates SIM every step or never are replayed from
+ * one CUDA graph holding all n lattices' steps: one host launch per 32 n
+ * lattice steps.  The rest are queued step by step.  The parameter studies
+ * of Sec. 4 (one lattice per angle of attack, per estimator, per resolution)
+ * are such batches; the paper itself steps one lattice at a time. */
+typedef struct vplbm_batch vplbm_batch;
+
+/* ctxs: host array of n >= 1 distinct contexts created on the current device.
+ * The batch keeps the pointers: destroy it before any of its contexts.
+ * cuda_stream: the stream the batch's steps are queued on; each
+ * vplbm_batch_step first orders that stream after every lattice's own stream
+ * and afterwards orders every lattice's own stream after it.  EINVAL for an
+ * empty list, a NULL or repeated context, or a context of another device.
+ * Failures of the batch calls are reported through vplbm_last_error(NULL). */
+vplbm_status vplbm_batch_create(vplbm_ctx *const *ctxs, int32_t n, void *cuda_stream,
+                                vplbm_batch **out);
+
+/* Queues nsteps time steps (nsteps >= 0) of every lattice of the batch, each
+ * step as vplbm_step defines it.  ESTATE when a lattice has no body placed
+ * (nothing is queued then).  A vplbm_set_body on a member between calls is
+ * seen by the next call. */
+vplbm_status vplbm_batch_step(vplbm_batch *batch, int32_t nsteps);
+
+/* Releases the batch (never its contexts).  NULL is accepted. */
+void vplbm_batch_destroy(vplbm_batch *batch);
+
 /* The SIM force (F[0], F[1], T about ref) of a state the caller supplies,
  * computed without any device allocation by the caller or the library.  For
  * callers that cannot allocate device memory: code embedded in a host

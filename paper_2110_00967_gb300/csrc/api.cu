@@ -227,6 +227,7 @@ struct vplbm_ctx {
   int sim_every = 0;  // effective
   long long steps = 0;
   int64_t launches = 0;
+  uint64_t generation = 0;  // bumped whenever captured step graphs go stale
   cudaGraphExec_t graph = nullptr;  // 2 * kGraphPairs steps starting from buffer 0
   cudaStream_t side = nullptr;      // the special kernel's stream
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -616,6 +617,7 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
+  ++c->generation;
   cudaStream_t s = c->stream;
   c->region_host = reg;
   for (int k = 0; k < 2; ++k) {
@@ -651,7 +653,7 @@ vplbm_status vplbm_step(vplbm_ctx *c, int32_t nsteps) {
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "no body placed (vplbm_set_body)");
   cudaStream_t s = c->stream;
   int left = nsteps;
-  const bool graphable = s != nullptr && (c->sim_every <= 1);
+  const bool graphable = c->sim_every <= 1;
   while (left > 0) {
     if (graphable && !c->pre && c->cur == 0 && left >= 2 * kGraphPairs) {
       if (vplbm_status st = ensure_graph(c)) return st;
@@ -855,5 +857,180 @@ void vplbm_destroy(vplbm_ctx *c) {
 }
 
 const char *vplbm_last_error(const vplbm_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+
+struct vplbm_batch {
+  std::vector<vplbm_ctx *> ctxs;
+  std::vector<uint64_t> generations;  // of the contexts when the graph was captured
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;  // 2 * kGraphPairs steps of every lattice from buffer 0
+  std::vector<cudaEvent_t> ev_in;   // each lattice's stream -> the batch stream
+  cudaEvent_t ev_out = nullptr;     // the batch stream -> each lattice's stream
+};
+
+namespace {
+
+vplbm_status batch_fail(vplbm_status st, const std::string &msg) {
+  g_err = msg;
+  return st;
+}
+
+vplbm_status batch_cuda(cudaError_t e, const char *where) {
+  return batch_fail(VPLBM_ECUDA, fmt("%s: %s", where, cudaGetErrorString(e)));
+}
+
+// a failure of a per-lattice call, reported through the global text
+vplbm_status batch_ctx_fail(vplbm_status st, int k, const vplbm_ctx *c) {
+  return batch_fail(st, fmt("lattice %d: %s", k, c->err.c_str()));
+}
+
+void batch_drop_graph(vplbm_batch *b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+}
+
+// One graph holding 2 * kGraphPairs steps of every lattice, round-robin
+// (step k of lattice 0, ..., of lattice n-1, then step k+1), each lattice
+// starting from buffer 0.
+vplbm_status batch_capture(vplbm_batch *b) {
+  batch_drop_graph(b);
+  if (!b->capture_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return batch_cuda(e, "cudaStreamCreateWithFlags");
+  }
+  std::vector<int64_t> launches;
+  for (vplbm_ctx *c : b->ctxs) launches.push_back(c->launches);
+  cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return batch_cuda(e, "cudaStreamBeginCapture");
+  for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
+    for (size_t q = 0; q < b->ctxs.size() && e == cudaSuccess; ++q) {
+      vplbm_ctx *c = b->ctxs[q];
+      e = queue_step(c, b->capture_stream, k & 1, false, c->sim_every == 1 && c->n_sim > 0);
+    }
+  for (size_t q = 0; q < b->ctxs.size(); ++q) b->ctxs[q]->launches = launches[q];
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return batch_cuda(e, "capture of the batch graph");
+  }
+  if (e2 != cudaSuccess) return batch_cuda(e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return batch_cuda(e, "cudaGraphInstantiate");
+  }
+  b->generations.clear();
+  for (vplbm_ctx *c : b->ctxs) b->generations.push_back(c->generation);
+  return VPLBM_OK;
+}
+
+bool batch_graph_current(const vplbm_batch *b) {
+  if (!b->graph) return false;
+  for (size_t q = 0; q < b->ctxs.size(); ++q)
+    if (b->ctxs[q]->generation != b->generations[q]) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+vplbm_status vplbm_batch_create(vplbm_ctx *const *ctxs, int32_t n, void *cuda_stream,
+                                vplbm_batch **out) {
+  if (!out) return batch_fail(VPLBM_EINVAL, "vplbm_batch_create: out is NULL");
+  *out = nullptr;
+  if (!ctxs || n < 1) return batch_fail(VPLBM_EINVAL, "vplbm_batch_create: no lattices");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess)
+    return batch_fail(VPLBM_ECUDA, "vplbm_batch_create: no current device");
+  for (int k = 0; k < n; ++k) {
+    if (!ctxs[k]) return batch_fail(VPLBM_EINVAL, fmt("vplbm_batch_create: lattice %d is NULL", k));
+    for (int q = 0; q < k; ++q)
+      if (ctxs[q] == ctxs[k])
+        return batch_fail(VPLBM_EINVAL, fmt("vplbm_batch_create: lattice %d repeats lattice %d", k, q));
+    if (ctxs[k]->device != dev)
+      return batch_fail(VPLBM_EINVAL, fmt("vplbm_batch_create: lattice %d is on device %d, not the current %d",
+                                          k, ctxs[k]->device, dev));
+  }
+  vplbm_batch *b = new vplbm_batch;
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->ev_in.assign(n, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < n && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&b->ev_in[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    vplbm_batch_destroy(b);
+    return batch_cuda(e, "vplbm_batch_create: cudaEventCreateWithFlags");
+  }
+  *out = b;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
+  if (!b) return batch_fail(VPLBM_EINVAL, "vplbm_batch_step: batch is NULL");
+  if (nsteps < 0) return batch_fail(VPLBM_EINVAL, "vplbm_batch_step: nsteps must be >= 0");
+  const int n = (int)b->ctxs.size();
+  for (int k = 0; k < n; ++k)
+    if (!b->ctxs[k]->has_body)
+      return batch_fail(VPLBM_ESTATE, fmt("vplbm_batch_step: lattice %d has no body placed", k));
+  if (nsteps == 0) return VPLBM_OK;
+  cudaStream_t s = b->stream;
+  // the batch's work follows what each lattice's own stream holds
+  for (int k = 0; k < n; ++k) {
+    vplbm_ctx *c = b->ctxs[k];
+    if (c->stream == s) continue;
+    cudaError_t e = cudaEventRecord(b->ev_in[k], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_in[k], 0);
+    if (e != cudaSuccess) return batch_cuda(e, "vplbm_batch_step: ordering after a lattice stream");
+  }
+  bool graphable = true;
+  for (vplbm_ctx *c : b->ctxs) graphable = graphable && c->sim_every <= 1;
+  int left = nsteps;
+  while (left > 0) {
+    bool aligned = graphable && left >= 2 * kGraphPairs;
+    for (vplbm_ctx *c : b->ctxs) aligned = aligned && !c->pre && c->cur == 0;
+    if (aligned) {
+      if (!batch_graph_current(b))
+        if (vplbm_status st = batch_capture(b)) return st;
+      const cudaError_t e = cudaGraphLaunch(b->graph, s);
+      if (e != cudaSuccess) return batch_cuda(e, "vplbm_batch_step: cudaGraphLaunch");
+      for (vplbm_ctx *c : b->ctxs) {
+        c->launches += 4 * kGraphPairs;
+        c->steps += 2 * kGraphPairs;
+      }
+      left -= 2 * kGraphPairs;
+      continue;
+    }
+    for (int k = 0; k < n; ++k)
+      if (vplbm_status st = one_step(b->ctxs[k], s)) return batch_ctx_fail(st, k, b->ctxs[k]);
+    --left;
+  }
+  // and each lattice's own stream follows the batch's work
+  cudaError_t e = cudaEventRecord(b->ev_out, s);
+  for (int k = 0; k < n && e == cudaSuccess; ++k)
+    if (b->ctxs[k]->stream != s) e = cudaStreamWaitEvent(b->ctxs[k]->stream, b->ev_out, 0);
+  if (e != cudaSuccess) return batch_cuda(e, "vplbm_batch_step: ordering of the lattice streams");
+  return VPLBM_OK;
+}
+
+void vplbm_batch_destroy(vplbm_batch *b) {
+  if (!b) return;
+  batch_drop_graph(b);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  for (cudaEvent_t ev : b->ev_in)
+    if (ev) cudaEventDestroy(ev);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  delete b;
+}
 
 }  // extern "C"

@@ -587,10 +587,6 @@ template <typename S, bool kForce>
 __global__ void __launch_bounds__(kThreads) bulk_kernel(const StepArgs p) {
   using T = typename Store<S>::T;
   const int ti = blockIdx.x, tj = blockIdx.y;
-  {
-    const ForceRegion reg = *p.reg_src;
-    if (ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1) return;
-  }
   const Lattice &L = p.L;
   const int i = ti * kTileX + threadIdx.x;
   const int j = tj * kTileY + threadIdx.y;
@@ -598,10 +594,16 @@ __global__ void __launch_bounds__(kThreads) bulk_kernel(const StepArgs p) {
   const S *__restrict__ src = static_cast<const S *>(p.src);
   S *__restrict__ dst = static_cast<S *>(p.dst);
   const int64_t node = (int64_t)j * L.pitch + i;
+  // the populations are requested before the force-region bounds are known,
+  // so that their latency is not added to that of the bounds
   T h[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a)
     h[a] = Store<S>::ld(src + (int64_t)a * L.plane + node - cy_of(a) * L.pitch - cx_of(a));
+  {
+    const ForceRegion reg = *p.reg_src;
+    if (ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1) return;  // special kernel
+  }
   const Consts<T> cst(p);
   const T drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
   const T rho = (T)1 + drho;

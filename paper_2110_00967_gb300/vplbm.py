@@ -108,6 +108,9 @@ _SIGS = [
     ("vplbm_get_sim_nodes", [_vp, _P(C.c_int32), C.c_int32, _P(C.c_int32)], C.c_int),
     ("vplbm_check", [_vp], C.c_int),
     ("vplbm_launch_count", [_vp, _P(C.c_int64)], C.c_int),
+    ("vplbm_batch_create", [_P(_vp), C.c_int32, _vp, _P(_vp)], C.c_int),
+    ("vplbm_batch_step", [_vp, C.c_int32], C.c_int),
+    ("vplbm_batch_destroy", [_vp], None),
     ("vplbm_sim_force_static", [_P(vplbm_config), _vp, _vp, C.c_int32, _P(C.c_double),
                                 _P(C.c_double), _P(C.c_double), _vp], C.c_int),
     ("vplbm_destroy", [_vp], None),
@@ -255,6 +258,21 @@ def vplbm_launch_count(ctx) -> int:
     n = C.c_int64()
     _check(lib().vplbm_launch_count(ctx, C.byref(n)), ctx)
     return n.value
+
+
+def vplbm_batch_create(ctxs, stream: int):
+    arr = (_vp * len(ctxs))(*ctxs)
+    b = _vp()
+    _check(lib().vplbm_batch_create(arr, len(ctxs), stream, C.byref(b)))
+    return b
+
+
+def vplbm_batch_step(batch, nsteps: int):
+    _check(lib().vplbm_batch_step(batch, nsteps))
+
+
+def vplbm_batch_destroy(batch):
+    lib().vplbm_batch_destroy(batch)
 
 
 def vplbm_sim_force_static(cfg: vplbm_config, f_dev_ptr: int, chi_dev_ptr: int, pts, ref,
@@ -413,3 +431,39 @@ def body_of(w) -> vplbm_body:
                 moving=1 if b.moving else 0, density_ratio=b.density_ratio,
                 gravity=b.gravity, n_sim_points=b.n_sim_points,
                 estimator=SIM if b.estimator == "sim" else MEM)
+
+
+# ---------------------------------------------------------------------------
+# several lattices stepped together
+# ---------------------------------------------------------------------------
+class Batch:
+    """Lattices stepped in lockstep on one stream (vplbm_batch_*).  Keeps the
+    Lattice objects alive; close() (or garbage collection) releases the batch
+    before them."""
+
+    def __init__(self, lattices, stream=None):
+        import torch
+        self.lattices = list(lattices)
+        dev = self.lattices[0].device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        with torch.cuda.device(dev):
+            self.handle = vplbm_batch_create([l.ctx for l in self.lattices],
+                                             self.stream.cuda_stream)
+
+    def step(self, n: int = 1):
+        vplbm_batch_step(self.handle, n)
+
+    @property
+    def launches(self) -> int:
+        return sum(l.launches for l in self.lattices)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            vplbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

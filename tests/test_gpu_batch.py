@@ -1,0 +1,139 @@
+"""Batches (vplbm_batch_*): several lattices stepped in lockstep on one stream,
+runs of 32 steps replayed from one CUDA graph.  The lattices share no data, so
+every member must end bit-identical -- state, force histories, sums, body --
+to the same lattice stepped alone."""
+import numpy as np
+import pytest
+
+from paper_2110_00967_gb300 import vplbm as V
+from paper_2110_00967_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "the GPU tests need a CUDA device"
+    V.lib()
+    yield
+
+
+def lattice(w, **over):
+    lat = V.Lattice(V.config_of(w, **over))
+    lat.set_body(V.body_of(w))
+    return lat
+
+
+def falling_disk(est):
+    return W.Workload(name="fall", nx=48, ny=96, dtype="f64", collision="trt", tau_plus=0.6,
+                      u_in=(0.0, 0.0), bc=("noslip",) * 4,
+                      body=W.Body("disk", length=12.0, x_c=20.3, y_c=70.0, moving=True,
+                                  density_ratio=1.5, gravity=(0.0, -6e-4), estimator=est),
+                      steps=100)
+
+
+MEMBERS = [
+    lambda: (W.disk_channel(), {}),
+    lambda: (W.naca(10.0, dtype="f32", nx=512, ny=256), {}),
+    lambda: (W.naca(5.0, dtype="f16", nx=256, ny=128), {}),
+    lambda: (falling_disk("sim"), {}),
+]
+
+
+def same_state(a, b, n):
+    assert np.array_equal(a.get_f(), b.get_f())
+    assert a.steps == b.steps == n
+    for est in (V.MEM, V.SIM):
+        try:
+            ha = a.history(est, min(n, 64))
+        except V.VplbmError:
+            continue
+        np.testing.assert_array_equal(ha, b.history(est, min(n, 64)))
+    sa, na = a.sums()
+    sb, nb = b.sums()
+    np.testing.assert_array_equal(sa, sb)
+    np.testing.assert_array_equal(na, nb)
+    np.testing.assert_array_equal(a.get_body(), b.get_body())
+    assert np.array_equal(a.get_mask(), b.get_mask())
+
+
+def test_batch_equals_each_lattice_alone():
+    ws = [m() for m in MEMBERS]
+    alone = [lattice(w, **o) for w, o in ws]
+    batched = [lattice(w, **o) for w, o in ws]
+    batch = V.Batch(batched)
+    for n in (1, 69, 32, 3):  # the pre step, graph runs, an odd level, single steps
+        batch.step(n)
+        for lat in alone:
+            lat.step(n)
+    total = 105
+    for a, b in zip(alone, batched):
+        same_state(a, b, total)
+    # the same kernels ran, whether from the batch graph or one by one
+    assert batch.launches == sum(l.launches for l in alone)
+    batch.close()
+
+
+def test_batch_with_sparse_sim_steps_one_by_one():
+    w = W.naca(15.0, dtype="f32", nx=256, ny=128)
+    a, b = lattice(w, sim_every=3), lattice(w, sim_every=3)
+    c, d = lattice(W.disk_channel()), lattice(W.disk_channel())
+    batch = V.Batch([b, d])
+    batch.step(70)
+    a.step(70)
+    c.step(70)
+    same_state(a, b, 70)
+    same_state(c, d, 70)
+
+
+def test_set_body_between_batch_steps_is_seen():
+    w0 = W.naca(0.0, dtype="f32", nx=256, ny=128)
+    w1 = W.naca(12.0, dtype="f32", nx=256, ny=128)
+    a, b = lattice(w0), lattice(w0)
+    other_a, other_b = lattice(W.disk_channel()), lattice(W.disk_channel())
+    batch = V.Batch([b, other_b])
+    batch.step(65)
+    a.step(65)
+    other_a.step(65)
+    for lat in (a, b):
+        lat.set_body(V.body_of(w1))  # restarts the solve around the new body
+    batch.step(66)
+    a.step(66)
+    other_a.step(66)
+    same_state(a, b, 66)
+    same_state(other_a, other_b, 131)
+
+
+def test_batch_on_a_separate_stream_is_ordered():
+    import torch
+    w = W.naca(8.0, dtype="f32", nx=256, ny=128)
+    a, b = lattice(w), lattice(w)
+    s = torch.cuda.Stream()
+    batch = V.Batch([b], stream=s)
+    batch.step(40)
+    a.step(40)
+    # b's own stream (the default one) reads after the batch's steps
+    same_state(a, b, 40)
+
+
+def test_batch_errors():
+    w = W.naca(0.0, nx=256, ny=128)
+    lat = lattice(w)
+    with pytest.raises(V.VplbmError) as e:
+        V.vplbm_batch_create([], 0)
+    assert e.value.status == V.EINVAL
+    with pytest.raises(V.VplbmError) as e:
+        V.vplbm_batch_create([lat.ctx, lat.ctx], 0)
+    assert e.value.status == V.EINVAL and "repeats" in V.vplbm_last_error(None)
+    bare = V.Lattice(V.config_of(w))  # no body placed
+    batch = V.Batch([lat, bare])
+    with pytest.raises(V.VplbmError) as e:
+        batch.step(1)
+    assert e.value.status == V.ESTATE
+    assert lat.steps == 0  # nothing was queued
+    with pytest.raises(V.VplbmError) as e:
+        V.vplbm_batch_step(batch.handle, -1)
+    assert e.value.status == V.EINVAL
+    batch.close()
+    V.vplbm_batch_destroy(None)
