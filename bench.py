@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 ANGLES = (0.0, 5.0, 10.0, 15.0, 20.0)
 NX, NY = 2048, 1024
-BYTES_PER_LUP = 9 * 4 + 9 * 4 + 1  # FP32 populations read + written, mask byte
+BYTES_PER_LUP = 9 * 4 + 9 * 4  # FP32 populations read once and written once
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_naca2048_f32.md")
 KERNEL_SOURCES = ("paper_2110_00967_gb300/csrc/step.cu",
                   "paper_2110_00967_gb300/csrc/vplbm_internal.cuh",

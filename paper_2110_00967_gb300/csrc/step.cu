@@ -301,11 +301,17 @@ __device__ void tail_reraster(const StepArgs &p, const BodyState &old_b, const B
 
 // The last participating block: the step's forces from the fixed-point sums
 // (plus the polygon's constant SIM part), histories, running sums, body.
+// Its loads are spread over threads and issued together, and each thread then
+// stores its own words: the tail costs a few memory round trips, not one per
+// word.
 template <typename T>
 __device__ void tail(const StepArgs &p, const ForceRegion &reg) {
+  constexpr int kBodyWords = (int)(sizeof(BodyState) / sizeof(unsigned long long));
+  static_assert(sizeof(BodyState) % sizeof(unsigned long long) == 0, "BodyState in 8-byte words");
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   __shared__ double tot[kAccSlots];
   __shared__ BodyState old_b, new_b;
+  __shared__ long long step_s;
   const bool do_sim = p.sim_blocks > 0;
   if (tid < kAccSlots) {
     // the sums were added by other SMs: read them through L2
@@ -314,20 +320,23 @@ __device__ void tail(const StepArgs &p, const ForceRegion &reg) {
     double v = Fix<T>::value(w0, w1);
     if (tid >= 3) v += p.sim_const[tid - 3];
     tot[tid] = v;
+  } else if (tid >= 32 && tid < 32 + kBodyWords) {
+    reinterpret_cast<unsigned long long *>(&old_b)[tid - 32] =
+        __ldcg(reinterpret_cast<const unsigned long long *>(p.body_src) + (tid - 32));
+  } else if (tid == 64) {
+    step_s = __ldcg(p.dev_step);
   }
   __syncthreads();
-  if (tid == 0) {
-    const long long step = *p.dev_step;
-    double *h = p.hist + 6 * (step % p.hist_len);
-    for (int k = 0; k < 3; ++k) h[k] = tot[k];
-    for (int k = 3; k < 6; ++k) h[k] = do_sim ? tot[k] : __longlong_as_double(0x7ff8000000000000LL);
-    for (int k = 0; k < 3; ++k) p.sums[k] += tot[k];
+  if (tid < 6) {
+    const bool have = tid < 3 || do_sim;
+    p.hist[6 * (step_s % p.hist_len) + tid] =
+        have ? tot[tid] : __longlong_as_double(0x7ff8000000000000LL);
+    if (have) p.sums[tid] += tot[tid];
+  } else if (tid == 6) {
     p.counts[0] += 1;
-    if (do_sim) {
-      for (int k = 3; k < 6; ++k) p.sums[k] += tot[k];
-      p.counts[1] += 1;
-    }
-    old_b = *p.body_src;
+  } else if (tid == 7 && do_sim) {
+    p.counts[1] += 1;
+  } else if (tid == 32) {
     new_b = old_b;
     ForceRegion nreg = reg;
     if (old_b.moving) {
@@ -345,10 +354,13 @@ __device__ void tail(const StepArgs &p, const ForceRegion &reg) {
         nreg = reg;
       }
     }
-    *p.body_dst = new_b;
     *p.reg_dst = nreg;
-    *p.dev_step = step + 1;
+    *p.dev_step = step_s + 1;
   }
+  __syncthreads();
+  if (tid >= 32 && tid < 32 + kBodyWords)
+    reinterpret_cast<unsigned long long *>(p.body_dst)[tid - 32] =
+        reinterpret_cast<const unsigned long long *>(&new_b)[tid - 32];
   __syncthreads();
   if (old_b.moving && (new_b.xg != old_b.xg || new_b.yg != old_b.yg)) tail_reraster(p, old_b, new_b);
   __syncthreads();
