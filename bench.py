@@ -36,7 +36,10 @@ sys.path.insert(0, ROOT)
 
 ANGLES = (0.0, 5.0, 10.0, 15.0, 20.0)
 NX, NY = 2048, 1024
-BYTES_PER_LUP = 9 * 4 + 9 * 4  # FP32 populations read once and written once
+# populations read once and written once per node: 9 x 4 B + 9 x 4 B for FP32 storage,
+# 9 x 2 B + 9 x 2 B for the 16-bit offset forms
+BYTES_PER_LUP = {"f32": 72, "f16": 36, "bf16": 36}
+STORAGE_NAME = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_naca2048_f32.md")
 KERNEL_SOURCES = ("paper_2110_00967_gb300/csrc/step.cu",
                   "paper_2110_00967_gb300/csrc/vplbm_internal.cuh",
@@ -44,14 +47,17 @@ KERNEL_SOURCES = ("paper_2110_00967_gb300/csrc/step.cu",
 METRIC = "VP-LBM MLUPS"
 CHUNK = 32  # steps per graph replay of the batch
 HISTORY = 64  # force-history ring of each lattice
-WORKLOAD = "naca0012-re1000-2048x1024-f32-alpha0,5,10,15,20"
+def workload_name(dtype: str) -> str:
+    return f"naca0012-re1000-2048x1024-{dtype}-alpha0,5,10,15,20"
 
 
-def config_block(extra=None):
-    c = {"workload": WORKLOAD, "grid": [NX, NY], "instances": len(ANGLES), "chord": 200,
-         "reynolds": 1000, "tau_plus": 0.53, "collision": "trt-lambda-1/6",
+def config_block(dtype: str = "f32", extra=None):
+    mb = 151 if dtype == "f32" else 75
+    c = {"workload": workload_name(dtype), "grid": [NX, NY], "instances": len(ANGLES),
+         "chord": 200, "reynolds": 1000, "tau_plus": 0.53, "collision": "trt-lambda-1/6",
+         "storage": "f32" if dtype == "f32" else f"{dtype} offsets from feq(1, u_in)",
          "forces_per_step": ["mem", "sim-849"],
-         "l2": "inputs larger than L2: 5 lattices x 151 MB ping-pong, stepped in turn"}
+         "l2": f"inputs larger than L2: 5 lattices x {mb} MB ping-pong, stepped in turn"}
     if extra:
         c.update(extra)
     return c
@@ -65,9 +71,11 @@ def kernel_sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(dtype: str = "f32"):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source."""
+    if it was taken on the current kernel source (FP32 storage only)."""
+    if dtype != "f32":
+        return None
     try:
         text = open(PROFILE).read()
     except OSError:
@@ -218,7 +226,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    works = [W.naca(a, dtype="f32") for a in ANGLES]
+    works = [W.naca(a, dtype=args.dtype) for a in ANGLES]
     lats = [V.Lattice(V.config_of(w, history_len=HISTORY), device=dev) for w in works]
     for w, lat in zip(works, lats):
         lat.set_body(V.body_of(w))
@@ -252,7 +260,7 @@ def run_ours(args, rank, world, local_rank):
     # (geometry and body state up), step, and read every step's forces back
     # (MEM and SIM, 32 steps at a time) into pinned host memory
     e2e_steps = max(2 * CHUNK, min(args.steps, 2000) // CHUNK * CHUNK)
-    pinned = torch.empty((len(lats), e2e_steps, 2, CHUNK, 3), dtype=torch.float64,
+    pinned = torch.empty((len(lats), e2e_steps // CHUNK, 2, CHUNK, 3), dtype=torch.float64,
                          pin_memory=True).numpy()
     torch.cuda.synchronize()
     barrier(world)
@@ -266,19 +274,21 @@ def run_ours(args, rank, world, local_rank):
             pinned[i, c, 1] = lat.history(V.SIM, CHUNK)
     torch.cuda.synchronize()
     e2e_dt = reduce_max(time.perf_counter() - t0, world, dev)
-    assert np.isfinite(pinned[:, : e2e_steps // CHUNK]).all()
-    body_bytes = 16 * 8 + 4 * 4  # device body state block
-    sim_bytes = 849 * 48
-    h2d = len(lats) * (body_bytes + sim_bytes) / e2e_steps
-    d2h = len(lats) * 6 * 8
+    assert np.isfinite(pinned).all()
+    # host -> device per lattice and set_body: the body state and the force region (two
+    # buffers each, 152 and 24 bytes) and the 849 SIM points (64 bytes each)
+    h2d = len(lats) * (2 * 152 + 2 * 24 + 849 * 64) / e2e_steps
+    # device -> host per lattice and step: one history row (6 doubles) per estimator read
+    d2h = len(lats) * 2 * 6 * 8
     batch.close()
 
     nodes = NX * NY * len(lats)
     value = world * nodes * args.steps / (elapsed_ms / 1e3) / 1e6
     e2e_value = world * nodes * e2e_steps / e2e_dt / 1e6
     peak, peak_kind = measured_hbm_peak()
-    achieved = BYTES_PER_LUP * NX * NY / (lattice_step_ms / 1e3) / 1e9
-    traffic = profiled_traffic()
+    bpl = BYTES_PER_LUP[args.dtype]
+    achieved = bpl * NX * NY / (lattice_step_ms / 1e3) / 1e9
+    traffic = profiled_traffic(args.dtype)
     if rank != 0:
         return None
     line = {
@@ -286,13 +296,14 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed_ms / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_block({"parallelism": f"replicas{world}"}),
+        "config": config_block(args.dtype, {"parallelism": f"replicas{world}"}),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "one lattice step: bulk_kernel<float> with special_kernel<float> "
-                               "beside it, timed over the region",
+                     "kernel": f"one lattice step: bulk_kernel<{STORAGE_NAME[args.dtype]}> with "
+                               f"special_kernel<{STORAGE_NAME[args.dtype]}> beside it, timed over "
+                               "the region",
                      "kernel_avg_us": round(lattice_step_ms * 1e3, 3),
-                     "bytes_per_lup": BYTES_PER_LUP, "peak_kind": peak_kind},
+                     "bytes_per_lup": bpl, "peak_kind": peak_kind},
         "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
@@ -313,8 +324,8 @@ def run_reference(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_block({"reference_sample": "one step of the 10-degree lattice per "
-                                                    "benchmark step"}),
+        "config": config_block(args.dtype, {"reference_sample": "one step of the 10-degree "
+                                                                "lattice per benchmark step"}),
         "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores,
                          "kind": "oracle",
                          "sample": f"{args.steps} steps of the 10-degree 2048x1024 lattice"},
@@ -330,6 +341,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dtype", choices=("f32", "f16", "bf16"), default="f32",
+                    help="population storage: FP32, or FP16/BF16 offsets (FP32 collision)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

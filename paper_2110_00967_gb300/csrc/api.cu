@@ -725,14 +725,20 @@ vplbm_status vplbm_force_history(vplbm_ctx *c, int32_t estimator, int32_t count,
   if (!out || count < 0 || count > len || count > c->steps)
     return fail(c, VPLBM_EINVAL, "bad history request");
   if (estimator != VPLBM_MEM && estimator != VPLBM_SIM) return fail(c, VPLBM_EINVAL, "unknown estimator");
-  std::vector<double> all((size_t)len * 6);
-  VPLBM_CUDA(c, cudaMemcpyAsync(all.data(), c->hist, all.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (count == 0) return VPLBM_OK;
+  // the requested rows only: one copy, or two where they wrap around the ring
+  std::vector<double> rows((size_t)count * 6);
+  const int first = (int)((c->steps - count) % len);
+  const int n1 = std::min(count, len - first);
+  VPLBM_CUDA(c, cudaMemcpyAsync(rows.data(), c->hist + 6 * (size_t)first, (size_t)n1 * 6 * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+  if (count > n1)
+    VPLBM_CUDA(c, cudaMemcpyAsync(rows.data() + 6 * (size_t)n1, c->hist, (size_t)(count - n1) * 6 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream));
   if (vplbm_status st = sync(c)) return st;
   const int off = estimator == VPLBM_SIM ? 3 : 0;
-  for (int k = 0; k < count; ++k) {
-    const long long step = c->steps - count + k;
-    for (int q = 0; q < 3; ++q) out[3 * k + q] = all[6 * (step % len) + off + q];
-  }
+  for (int k = 0; k < count; ++k)
+    for (int q = 0; q < 3; ++q) out[3 * k + q] = rows[6 * (size_t)k + off + q];
   return VPLBM_OK;
 }
 

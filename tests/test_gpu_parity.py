@@ -353,6 +353,17 @@ def test_naca_full_size_sampled():
         assert np.abs(g[:2] - r[:2]).max() <= 1e-3 * np.abs(r[:2]).max()
 
 
+def test_history_ring_wraps():
+    """A short history ring that has wrapped returns the same last rows as a long one."""
+    w = W.naca(5.0, dtype="f32", nx=256, ny=128)
+    short, long_ = lattice(w, history_len=10), lattice(w, history_len=64)
+    short.step(37)
+    long_.step(37)
+    for est in (V.MEM, V.SIM):
+        np.testing.assert_array_equal(short.history(est, 10), long_.history(est, 37)[-10:])
+        np.testing.assert_array_equal(short.history(est, 3), long_.history(est, 37)[-3:])
+
+
 def test_graph_replay_equals_single_launches():
     w = W.naca(5.0, dtype="f32", nx=256, ny=128)
     a, b = lattice(w), lattice(w)
