@@ -253,6 +253,29 @@ def test_moving_disk_fp64_trajectory():
         assert rel_linf(lat.get_f(), f) <= 1e-10
 
 
+@pytest.mark.parametrize("est", ["mem", "sim"])
+def test_sedimentation_full_size_first_1000_steps(est):
+    """The 400 x 1600 sedimentation box (FP32 lattice, FP64 rigid body driven by
+    MEM or by SIM, chi re-rasterised every step) against the FP64 oracle over the
+    first 1000 steps: per-step forces within 1e-3 of the largest oracle force,
+    the body's velocity within 1e-3 relative and its position within 1e-4."""
+    w = W.sedimentation(est, steps=1000)
+    lat = lattice(w, history_len=1000)
+    lat.step(w.steps)
+    cfg, ob, chi, f, pts = oracle_setup(w)
+    mh, sh, bh, bad = o.run(cfg, ob, f, chi, w.steps, estimator=1 if est == "sim" else 0,
+                            sim_pts=pts)
+    assert bad == 0
+    ref = sh if est == "sim" else mh
+    got = lat.history(V.SIM if est == "sim" else V.MEM, w.steps)
+    scale = np.abs(ref[:, :2]).max()
+    assert np.abs(got[:, :2] - ref[:, :2]).max() <= 1e-3 * scale
+    b = lat.get_body()
+    assert abs(b[4] - bh[-1][4]) <= 1e-3 * abs(bh[-1][4])  # u_y
+    assert abs(b[1] - bh[-1][1]) <= 1e-4  # y
+    assert b[4] < 0 and b[1] < w.body.y_c  # it falls
+
+
 # ---------------------------------------------------------------------------
 # FP32 and 16-bit storage against the FP64 oracle
 # ---------------------------------------------------------------------------
