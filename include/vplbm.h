@@ -224,16 +224,19 @@ vplbm_status vplbm_launch_count(vplbm_ctx *ctx, int64_t *n);
 
 /* ---- batches: several lattices stepped together ----
  * A batch steps n independent lattices (any sizes and storage types, one
- * device) in lockstep on one stream: step k of lattice 0, of lattice 1, ...,
- * of lattice n-1, then step k+1.  Each lattice ends in the state, with the
- * force histories and sums, that stepping it alone would give (the lattices
- * share no data).  Runs of 32 steps in which every lattice starts from an
- * even time level since its last pre-collision state (vplbm_set_body or
- * vplbm_set_state) and evaluates SIM every step or never are replayed from
- * one CUDA graph holding all n lattices' steps: one host launch per 32 n
- * lattice steps.  The rest are queued step by step.  The parameter studies
- * of Sec. 4 (one lattice per angle of attack, per estimator, per resolution)
- * are such batches; the paper itself steps one lattice at a time. */
+ * device).  The lattices share no data, so each runs its steps on a stream of
+ * its own, forked from the batch's stream and joined back into it at the end
+ * of every vplbm_batch_step: steps of different lattices overlap, and one
+ * lattice's latency-bound work (force reductions, a moving body's update) runs
+ * while others use the memory bandwidth.  Each lattice ends in the state, with
+ * the force histories and sums, that stepping it alone would give.  Runs of
+ * 32 steps in which every lattice starts from an even time level since its
+ * last pre-collision state (vplbm_set_body or vplbm_set_state) and evaluates
+ * SIM every step or never are replayed from one CUDA graph holding all n
+ * lattices' steps: one host launch per 32 n lattice steps.  The rest are
+ * queued step by step.  The parameter studies of Sec. 4 (one lattice per
+ * angle of attack, per estimator, per resolution) are such batches; the paper
+ * itself steps one lattice at a time. */
 typedef struct vplbm_batch vplbm_batch;
 
 /* ctxs: host array of n >= 1 distinct contexts created on the current device.

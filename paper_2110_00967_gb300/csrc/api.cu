@@ -878,6 +878,9 @@ struct vplbm_batch {
   cudaGraphExec_t graph = nullptr;  // 2 * kGraphPairs steps of every lattice from buffer 0
   std::vector<cudaEvent_t> ev_in;   // each lattice's stream -> the batch stream
   cudaEvent_t ev_out = nullptr;     // the batch stream -> each lattice's stream
+  std::vector<cudaStream_t> chain;  // one stream per lattice: the lattices' steps run side by side
+  std::vector<cudaEvent_t> ev_chain;  // end of each chain -> the batch (or capture) stream
+  cudaEvent_t ev_fork = nullptr;      // start of a call on the batch (or capture) stream
 };
 
 namespace {
@@ -901,9 +904,28 @@ void batch_drop_graph(vplbm_batch *b) {
   b->graph = nullptr;
 }
 
-// One graph holding 2 * kGraphPairs steps of every lattice, round-robin
-// (step k of lattice 0, ..., of lattice n-1, then step k+1), each lattice
-// starting from buffer 0.
+// The lattices share no data, so each runs its steps on a stream of its own
+// (its chain), forked from s and joined back into s: the steps of different
+// lattices overlap, and one lattice's latency-bound special kernel runs while
+// other lattices' bulk kernels use the memory bandwidth.
+cudaError_t batch_fork(vplbm_batch *b, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(b->ev_fork, s);
+  for (size_t q = 0; q < b->chain.size() && e == cudaSuccess; ++q)
+    e = cudaStreamWaitEvent(b->chain[q], b->ev_fork, 0);
+  return e;
+}
+
+cudaError_t batch_join(vplbm_batch *b, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (size_t q = 0; q < b->chain.size() && e == cudaSuccess; ++q) {
+    e = cudaEventRecord(b->ev_chain[q], b->chain[q]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_chain[q], 0);
+  }
+  return e;
+}
+
+// One graph holding 2 * kGraphPairs steps of every lattice, each lattice on
+// its chain, each starting from buffer 0.
 vplbm_status batch_capture(vplbm_batch *b) {
   batch_drop_graph(b);
   if (!b->capture_stream) {
@@ -914,11 +936,13 @@ vplbm_status batch_capture(vplbm_batch *b) {
   for (vplbm_ctx *c : b->ctxs) launches.push_back(c->launches);
   cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return batch_cuda(e, "cudaStreamBeginCapture");
+  e = batch_fork(b, b->capture_stream);
   for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
     for (size_t q = 0; q < b->ctxs.size() && e == cudaSuccess; ++q) {
       vplbm_ctx *c = b->ctxs[q];
-      e = queue_step(c, b->capture_stream, k & 1, false, c->sim_every == 1 && c->n_sim > 0);
+      e = queue_step(c, b->chain[q], k & 1, false, c->sim_every == 1 && c->n_sim > 0);
     }
+  if (e == cudaSuccess) e = batch_join(b, b->capture_stream);
   for (size_t q = 0; q < b->ctxs.size(); ++q) b->ctxs[q]->launches = launches[q];
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
@@ -974,6 +998,13 @@ vplbm_status vplbm_batch_create(vplbm_ctx *const *ctxs, int32_t n, void *cuda_st
   for (int k = 0; k < n && e == cudaSuccess; ++k)
     e = cudaEventCreateWithFlags(&b->ev_in[k], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  b->chain.assign(n, nullptr);
+  b->ev_chain.assign(n, nullptr);
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->chain[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_chain[k], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     vplbm_batch_destroy(b);
     return batch_cuda(e, "vplbm_batch_create: cudaEventCreateWithFlags");
@@ -1017,8 +1048,12 @@ vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
       left -= 2 * kGraphPairs;
       continue;
     }
+    if (const cudaError_t e = batch_fork(b, s); e != cudaSuccess)
+      return batch_cuda(e, "vplbm_batch_step: forking the lattice chains");
     for (int k = 0; k < n; ++k)
-      if (vplbm_status st = one_step(b->ctxs[k], s)) return batch_ctx_fail(st, k, b->ctxs[k]);
+      if (vplbm_status st = one_step(b->ctxs[k], b->chain[k])) return batch_ctx_fail(st, k, b->ctxs[k]);
+    if (const cudaError_t e = batch_join(b, s); e != cudaSuccess)
+      return batch_cuda(e, "vplbm_batch_step: joining the lattice chains");
     --left;
   }
   // and each lattice's own stream follows the batch's work
@@ -1036,6 +1071,11 @@ void vplbm_batch_destroy(vplbm_batch *b) {
   for (cudaEvent_t ev : b->ev_in)
     if (ev) cudaEventDestroy(ev);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  for (cudaStream_t st : b->chain)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->ev_chain)
+    if (ev) cudaEventDestroy(ev);
   delete b;
 }
 
