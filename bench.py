@@ -392,6 +392,61 @@ def run_sedimentation(args, rank, world, local_rank):
     }
 
 
+def run_serving(args, rank, world, local_rank):
+    """A seeded mix of NACA 0012 solves served to convergence (continuous
+    batching under a memory budget); Poisson arrivals at 4 / (estimated mean
+    solve time of one request alone)."""
+    import torch
+    from paper_2110_00967_gb300 import serve as S
+    from paper_2110_00967_gb300 import vplbm as V
+    from paper_2110_00967_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    backend = S.GpuBackend(args.dtype, device=torch.device("cuda", local_rank))
+    # calibration: one 1024 x 512 request alone for two windows
+    probe = W.Request(-1, 0.0, 10.0, 1024, 512)
+    lat = backend.make(probe)
+    b = backend.batch([lat])
+    b.step(1000)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    b.step(1000)
+    torch.cuda.synchronize()
+    t_window = time.perf_counter() - t
+    b.close()
+    lat.close()
+    mean_nodes = sum(nx * ny for nx, ny in W.SERVING_GRIDS) / len(W.SERVING_GRIDS)
+    solve_s = t_window * (mean_nodes / (1024 * 512)) * (args.cap / 1000)
+    rate = 4.0 / solve_s
+    reqs = W.serving_requests(args.requests, rate=rate)
+    srv = S.Server(backend, memory_bytes=args.memory_gb << 30, window=1000, tol=1e-4,
+                   cap=args.cap, max_active=args.max_active)
+    barrier(world)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    torch.cuda.synchronize()
+    elapsed = reduce_max(time.perf_counter() - t0, world, torch.device("cuda", local_rank))
+    node_steps = sum(r.nx * r.ny * r.steps for r in res)
+    summ = S.summary(res, elapsed, node_steps)
+    if rank != 0:
+        return None
+    return {
+        "metric": "solves/s", "value": round(world * summ["solves_per_s"], 4), "unit": "solves/s",
+        "n_gpus": world, "steps": args.cap, "warmup": 1, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"naca0012-serving-{args.requests}req-seed2110-{args.dtype}",
+                   "grids": [list(g) for g in W.SERVING_GRIDS], "alpha_deg": [0, 20],
+                   "arrival_rate_per_s": round(rate, 4), "window": 1000, "tol": 1e-4,
+                   "cap_steps": args.cap, "memory_budget_gb": args.memory_gb,
+                   "max_active": args.max_active or "memory-bound",
+                   "parallelism": f"replicas{world}"},
+        "p50_s": round(summ["p50_s"], 4), "p99_s": round(summ["p99_s"], 4),
+        "converged": summ["converged"], "capped": summ["capped"],
+        "rejected": summ["rejected"], "aggregate_mlups": round(world * summ["mlups"], 1),
+        "elapsed_s": round(elapsed, 3),
+    }
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -422,9 +477,16 @@ def main(argv=None):
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu's "
                          "application-range replay, which measures the concurrent kernels "
                          "of the whole region)")
-    ap.add_argument("--workload", choices=("naca", "sedimentation"), default="naca",
+    ap.add_argument("--workload", choices=("naca", "sedimentation", "serving"), default="naca",
                     help="naca: the five NACA 0012 lattices (the benchmark); sedimentation: "
-                         "the 400 x 1600 falling-disk box, MEM and SIM runs")
+                         "the 400 x 1600 falling-disk box, MEM and SIM runs; serving: a seeded "
+                         "mix of NACA solves run to convergence")
+    ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
+    ap.add_argument("--cap", type=int, default=20000, help="serving: step cap per request")
+    ap.add_argument("--memory-gb", type=int, default=40, help="serving: device-memory budget")
+    ap.add_argument("--max-active", type=int, default=0,
+                    help="serving: most requests stepped at once (0: as many as fit; 1: one "
+                         "request at a time, the single-instance comparison)")
     ap.add_argument("--dtype", choices=("f32", "f16", "bf16"), default="f32",
                     help="population storage: FP32, or FP16/BF16 offsets (FP32 collision)")
     args = ap.parse_args(argv)
@@ -444,6 +506,8 @@ def main(argv=None):
         build()
         if args.workload == "sedimentation":
             line = run_sedimentation(args, rank, world, local_rank)
+        elif args.workload == "serving":
+            line = run_serving(args, rank, world, local_rank)
         else:
             line = run_ours(args, rank, world, local_rank)
     if line is not None:

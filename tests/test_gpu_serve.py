@@ -1,0 +1,49 @@
+"""The serving loop on the GPU: a request's result does not depend on what it
+is served with (lattices share no data), and its window-mean Cd/Cl match the
+FP64 oracle's means over the same steps within 1e-3."""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2110_00967_gb300 import serve as S
+from paper_2110_00967_gb300 import workloads as W
+from tests.helpers import oracle_setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "the GPU tests need a CUDA device"
+    yield
+
+
+def serve(reqs, cap):
+    srv = S.Server(S.GpuBackend("f32"), memory_bytes=8 << 30, window=1000, tol=1e-4, cap=cap)
+    return {r.rid: r for r in srv.run(reqs)}
+
+
+def test_result_alone_equals_result_in_a_mix():
+    target = W.Request(0, 0.0, 7.0, 512, 256)
+    mix = [target, W.Request(1, 0.0, 15.0, 768, 384), W.Request(2, 0.0, 2.0, 512, 256)]
+    alone = serve([target], cap=3000)[0]
+    mixed = serve(mix, cap=3000)[0]
+    assert alone.steps == mixed.steps == 3000
+    assert (alone.cd, alone.cl, alone.cd_sim, alone.cl_sim) == \
+        (mixed.cd, mixed.cl, mixed.cd_sim, mixed.cl_sim)
+
+
+def test_window_means_match_the_oracle():
+    req = W.Request(0, 0.0, 7.0, 512, 256)
+    got = serve([req], cap=3000)[0]
+    w = W.naca(7.0, dtype="f32", nx=512, ny=256, steps=3000)
+    cfg, body, chi, f, pts = oracle_setup(w)
+    mh, sh, _, bad = o.run(cfg, body, f, chi, 3000, sim_pts=pts)
+    assert bad == 0
+    chord = 512 * 200.0 / 2048.0
+    q = 0.5 * S.U0 ** 2 * chord
+    ref = (mh[2000:, 0].mean() / q, mh[2000:, 1].mean() / q,
+           sh[2000:, 0].mean() / q, sh[2000:, 1].mean() / q)
+    for g, r in zip((got.cd, got.cl, got.cd_sim, got.cl_sim), ref):
+        assert abs(g - r) <= 1e-3 * max(abs(r), 1e-2), (g, r)
