@@ -76,7 +76,7 @@ Layout make_layout(const vplbm_config &c) {
   l.dev_step = take(sizeof(long long));
   l.ticket = take(sizeof(unsigned int));
   l.status = take(sizeof(int32_t));
-  l.acc = take(kAccWords * sizeof(unsigned long long));
+  l.acc = take(2 * kAccWords * sizeof(unsigned long long));  // by step parity
   l.total = off;
   return l;
 }
@@ -219,6 +219,8 @@ struct vplbm_ctx {
   int32_t *status;
   int cur = 0;        // buffer holding the state
   bool pre = true;    // the state is a pre-collision field (first step reads in place)
+  bool pending = false;      // the last queued step's force sums still await finalizing
+  bool pending_sim = false;  // ... and that step evaluated SIM
   bool has_body = false;
   vplbm_body body_cfg{};
   BodyState body_host{};
@@ -275,7 +277,8 @@ StepArgs step_args(vplbm_ctx *c, int src, bool do_sim) {
   a.body_dst = c->body[1 - src];
   a.reg_src = c->region[src];
   a.reg_dst = c->region[1 - src];
-  a.acc = c->acc;
+  a.acc = c->acc + kAccWords * src;
+  a.acc_prev = c->acc + kAccWords * (1 - src);
   a.sim_pts = c->sim_pts;
   for (int k = 0; k < 3; ++k) a.sim_const[k] = c->sim_const[k];
   a.sim_nodes = c->sim_nodes;
@@ -321,13 +324,34 @@ bool sim_due(const vplbm_ctx *c, long long step) {
 // blocks) runs on the context's high-priority side stream beside the bulk
 // kernel (all other nodes, bandwidth-bound) on s; the two write disjoint
 // nodes, and s waits for both before the next step.
+// Finalizes the force sums of the last queued step if they were deferred: one
+// block on s (history row, running sums, step counter).
+cudaError_t flush_forces(vplbm_ctx *c, cudaStream_t s) {
+  if (!c->pending) return cudaSuccess;
+  StepArgs a = step_args(c, c->cur, false);  // acc_prev: the last step's sums
+  a.prev_sim = c->pending_sim ? 1 : 0;
+  c->pending = false;
+  ++c->launches;
+  return launch_finalize(c->cfg.dtype, a, s);
+}
+
 cudaError_t queue_step(vplbm_ctx *c, cudaStream_t s, int src, bool pre, bool do_sim) {
-  StepArgs a = step_args(c, src, do_sim);
   if (pre) {
+    cudaError_t e = flush_forces(c, s);
+    StepArgs a = step_args(c, src, do_sim);
     a.all_tiles = 1;
     ++c->launches;
-    return launch_special(c->cfg.dtype, false, a, s);
+    if (e == cudaSuccess) e = launch_special(c->cfg.dtype, false, a, s);
+    return e;
   }
+  StepArgs a = step_args(c, src, do_sim);
+  // a fixed body needs its force sums only after the call: the special kernel
+  // skips the ticket and tail, and the next step's special kernel (one extra
+  // block beside its work) or flush_forces finalizes them.  A moving body's
+  // update needs them within the step.
+  a.defer = c->body_host.moving ? 0 : 1;
+  a.finalize_prev = c->pending ? 1 : 0;
+  a.prev_sim = c->pending_sim ? 1 : 0;
   cudaError_t e = cudaEventRecord(c->ev_fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
   if (e == cudaSuccess) e = launch_special(c->cfg.dtype, true, a, c->side);
@@ -335,6 +359,8 @@ cudaError_t queue_step(vplbm_ctx *c, cudaStream_t s, int src, bool pre, bool do_
   if (e == cudaSuccess) e = launch_bulk(c->cfg.dtype, a, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
   c->launches += 2;
+  c->pending = a.defer != 0;
+  c->pending_sim = do_sim;
   return e;
 }
 
@@ -358,6 +384,7 @@ vplbm_status ensure_graph(vplbm_ctx *c) {
   const int64_t launches = c->launches;
   for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
     e = queue_step(c, c->capture_stream, k & 1, false, c->sim_every == 1 && c->n_sim > 0);
+  if (e == cudaSuccess) e = flush_forces(c, c->capture_stream);  // the graph ends finalized
   c->launches = launches;  // counted when the graph is launched
   cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
   if (e != cudaSuccess) {
@@ -643,6 +670,7 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
   c->cur = 0;
   c->pre = true;
   c->steps = 0;
+  c->pending = false;  // the accumulators were cleared with the other counters
   c->has_body = true;
   return sync(c);
 }
@@ -656,16 +684,19 @@ vplbm_status vplbm_step(vplbm_ctx *c, int32_t nsteps) {
   const bool graphable = c->sim_every <= 1;
   while (left > 0) {
     if (graphable && !c->pre && c->cur == 0 && left >= 2 * kGraphPairs) {
+      VPLBM_CUDA(c, flush_forces(c, s));  // a graph starts with nothing pending
       if (vplbm_status st = ensure_graph(c)) return st;
       VPLBM_CUDA(c, cudaGraphLaunch(c->graph, s));
-      c->launches += 4 * kGraphPairs;
+      c->launches += 4 * kGraphPairs + 1;
       c->steps += 2 * kGraphPairs;
+      c->pending = false;
       left -= 2 * kGraphPairs;
       continue;
     }
     if (vplbm_status st = one_step(c, s)) return st;
     --left;
   }
+  VPLBM_CUDA(c, flush_forces(c, s));  // every call returns with its forces finalized
   return VPLBM_OK;
 }
 
@@ -924,6 +955,18 @@ cudaError_t batch_join(vplbm_batch *b, cudaStream_t s) {
   return e;
 }
 
+// Finalizes the lattices' pending force sums, each on its chain.
+cudaError_t batch_flush(vplbm_batch *b, cudaStream_t s) {
+  bool any = false;
+  for (vplbm_ctx *c : b->ctxs) any = any || c->pending;
+  if (!any) return cudaSuccess;
+  cudaError_t e = batch_fork(b, s);
+  for (size_t q = 0; q < b->ctxs.size() && e == cudaSuccess; ++q)
+    e = flush_forces(b->ctxs[q], b->chain[q]);
+  if (e == cudaSuccess) e = batch_join(b, s);
+  return e;
+}
+
 // One graph holding 2 * kGraphPairs steps of every lattice, each lattice on
 // its chain, each starting from buffer 0.
 vplbm_status batch_capture(vplbm_batch *b) {
@@ -942,6 +985,8 @@ vplbm_status batch_capture(vplbm_batch *b) {
       vplbm_ctx *c = b->ctxs[q];
       e = queue_step(c, b->chain[q], k & 1, false, c->sim_every == 1 && c->n_sim > 0);
     }
+  for (size_t q = 0; q < b->ctxs.size() && e == cudaSuccess; ++q)
+    e = flush_forces(b->ctxs[q], b->chain[q]);  // the graph ends finalized
   if (e == cudaSuccess) e = batch_join(b, b->capture_stream);
   for (size_t q = 0; q < b->ctxs.size(); ++q) b->ctxs[q]->launches = launches[q];
   cudaGraph_t g = nullptr;
@@ -1037,13 +1082,17 @@ vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
     bool aligned = graphable && left >= 2 * kGraphPairs;
     for (vplbm_ctx *c : b->ctxs) aligned = aligned && !c->pre && c->cur == 0;
     if (aligned) {
+      // a graph starts with no lattice's force sums pending
+      if (const cudaError_t e = batch_flush(b, s); e != cudaSuccess)
+        return batch_cuda(e, "vplbm_batch_step: finalizing force sums");
       if (!batch_graph_current(b))
         if (vplbm_status st = batch_capture(b)) return st;
       const cudaError_t e = cudaGraphLaunch(b->graph, s);
       if (e != cudaSuccess) return batch_cuda(e, "vplbm_batch_step: cudaGraphLaunch");
       for (vplbm_ctx *c : b->ctxs) {
-        c->launches += 4 * kGraphPairs;
+        c->launches += 4 * kGraphPairs + 1;
         c->steps += 2 * kGraphPairs;
+        c->pending = false;
       }
       left -= 2 * kGraphPairs;
       continue;
@@ -1056,6 +1105,9 @@ vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
       return batch_cuda(e, "vplbm_batch_step: joining the lattice chains");
     --left;
   }
+  // every call returns with its forces finalized
+  if (const cudaError_t e = batch_flush(b, s); e != cudaSuccess)
+    return batch_cuda(e, "vplbm_batch_step: finalizing force sums");
   // and each lattice's own stream follows the batch's work
   cudaError_t e = cudaEventRecord(b->ev_out, s);
   for (int k = 0; k < n && e == cudaSuccess; ++k)

@@ -299,6 +299,42 @@ __device__ void tail_reraster(const StepArgs &p, const BodyState &old_b, const B
   }
 }
 
+// Force bookkeeping of a step whose tail was deferred (a fixed body): its
+// fixed-point sums (acc) become the step's history row and are added to the
+// running sums; the step counter advances and acc is cleared for reuse two
+// steps later.  Runs in one block beside the next step's work, or alone at
+// the end of a call.  Loads are spread over threads and issued together.
+template <typename T>
+__device__ void finalize(const StepArgs &p, unsigned long long *acc) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  __shared__ double tot[kAccSlots];
+  __shared__ long long step_s;
+  const bool do_sim = p.prev_sim != 0;
+  if (tid < kAccSlots) {
+    const long long w0 = (long long)__ldcg(acc + 2 * tid);
+    const long long w1 = (long long)__ldcg(acc + 2 * tid + 1);
+    double v = Fix<T>::value(w0, w1);
+    if (tid >= 3) v += p.sim_const[tid - 3];
+    tot[tid] = v;
+  } else if (tid == 64) {
+    step_s = __ldcg(p.dev_step);
+  }
+  __syncthreads();
+  if (tid < 6) {
+    const bool have = tid < 3 || do_sim;
+    p.hist[6 * (step_s % p.hist_len) + tid] =
+        have ? tot[tid] : __longlong_as_double(0x7ff8000000000000LL);
+    if (have) p.sums[tid] += tot[tid];
+  } else if (tid == 6) {
+    p.counts[0] += 1;
+  } else if (tid == 7 && do_sim) {
+    p.counts[1] += 1;
+  } else if (tid == 32) {
+    *p.dev_step = step_s + 1;
+  }
+  if (tid < kAccWords) acc[tid] = 0ull;  // every read of acc above precedes the barrier
+}
+
 // The last participating block: the step's forces from the fixed-point sums
 // (plus the polygon's constant SIM part), histories, running sums, body.
 // Its loads are spread over threads and issued together, and each thread then
@@ -523,6 +559,11 @@ __global__ void __launch_bounds__(kThreads) special_kernel(const StepArgs p) {
   const int tid = threadIdx.y * kTileX + threadIdx.x;
   const ForceRegion reg = *p.reg_src;
   const int b = blockIdx.x;
+  if (p.finalize_prev && b == (int)gridDim.x - 1) {
+    // the previous step's force sums, beside this step's work
+    finalize<T>(p, p.acc_prev);
+    return;
+  }
 
   if (b < p.sim_blocks) {
     // ---- SIM points of this level ----
@@ -576,6 +617,8 @@ __global__ void __launch_bounds__(kThreads) special_kernel(const StepArgs p) {
     if (!in_reg) return;  // uniform over the block
     warp_add(acc, p.acc, 0);
   }
+
+  if (p.defer) return;  // a later launch finalizes this step's sums
 
   // ---- ticket among the SIM blocks and the force-region tiles ----
   __syncthreads();
@@ -641,8 +684,14 @@ __global__ void __launch_bounds__(kThreads) bulk_kernel(const StepArgs p) {
 template <typename S, bool kGather>
 cudaError_t special_t(const StepArgs &a, cudaStream_t s) {
   const int tiles = a.all_tiles ? a.ntiles_x * a.ntiles_y : a.edge_blocks + a.region_slots;
-  special_kernel<S, kGather><<<a.sim_blocks + tiles, dim3(kTileX, kTileY), 0, s>>>(a);
+  special_kernel<S, kGather>
+      <<<a.sim_blocks + tiles + (a.finalize_prev ? 1 : 0), dim3(kTileX, kTileY), 0, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) finalize_kernel(const StepArgs p) {
+  finalize<T>(p, p.acc_prev);
 }
 
 template <typename S>
@@ -666,6 +715,14 @@ cudaError_t launch_special(int dtype, bool gather, const StepArgs &a, cudaStream
       return gather ? special_t<__nv_bfloat16, true>(a, s) : special_t<__nv_bfloat16, false>(a, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_finalize(int dtype, const StepArgs &a, cudaStream_t s) {
+  if (dtype == VPLBM_F64)
+    finalize_kernel<double><<<1, dim3(kTileX, kTileY), 0, s>>>(a);
+  else
+    finalize_kernel<float><<<1, dim3(kTileX, kTileY), 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_bulk(int dtype, const StepArgs &a, cudaStream_t s) {

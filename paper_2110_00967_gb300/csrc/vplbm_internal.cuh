@@ -409,7 +409,11 @@ struct StepArgs {
   BodyState *body_dst;         // body at level n + 1 (written by the tail)
   const ForceRegion *reg_src;
   ForceRegion *reg_dst;
-  unsigned long long *acc;  // [6][2] fixed-point sums of this step
+  unsigned long long *acc;       // [6][2] fixed-point sums of this step
+  unsigned long long *acc_prev;  // the previous step's sums (finalized by this launch)
+  int32_t defer;                 // 1: no ticket and tail; a later launch finalizes the sums
+  int32_t finalize_prev;         // 1: an extra last block finalizes acc_prev first
+  int32_t prev_sim;              // 1: the step being finalized evaluated SIM
   const SimPoint *sim_pts;
   int32_t *sim_nodes;    // [n_sim]
   int32_t n_sim;
@@ -524,6 +528,9 @@ void set_global_error(const std::string &msg);
 // the special kernel: SIM blocks, edge nodes, force-region tiles and the
 // FP64 tail (or every tile, with all_tiles set)
 cudaError_t launch_special(int dtype, bool gather, const StepArgs &a, cudaStream_t s);
+// one block that finalizes a deferred step's force sums (acc_prev): history
+// row, running sums, step counter
+cudaError_t launch_finalize(int dtype, const StepArgs &a, cudaStream_t s);
 // the bulk kernel: the nodes off the edges, outside the force-region tiles
 cudaError_t launch_bulk(int dtype, const StepArgs &a, cudaStream_t s);
 
