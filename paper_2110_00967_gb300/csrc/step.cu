@@ -681,6 +681,253 @@ __global__ void __launch_bounds__(kThreads) bulk_kernel(const StepArgs p) {
   if (!(rho > (T)0) || !isfinite(rho)) atomicOr(p.status, kStatusUnstable);
 }
 
+// ---------------------------------------------------------------------------
+// two nodes at once: the bulk kernel updates each thread's two nodes (rows r
+// and r + 1 of a tile) together.  FP32 uses the packed f32x2 instructions of
+// sm_100 and later (one instruction for both nodes); FP64 has no packed form
+// and runs the two nodes as separate scalar operations.
+// ---------------------------------------------------------------------------
+struct F2 {
+  float2 v;
+};
+__device__ __forceinline__ unsigned long long f2_bits(F2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.v.x), "f"(a.v.y));
+  return r;
+}
+__device__ __forceinline__ F2 bits_f2(unsigned long long r) {
+  F2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.v.x), "=f"(a.v.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ F2 vpair(float x, float y) { return F2{make_float2(x, y)}; }
+__device__ __forceinline__ F2 vsplat(float c) { return F2{make_float2(c, c)}; }
+__device__ __forceinline__ F2 vadd(F2 a, F2 b) { return F2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 vmul(F2 a, F2 b) { return F2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return F2{__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2 vsub(F2 a, F2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(r);
+}
+__device__ __forceinline__ F2 vrcp(F2 a) { return vpair(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
+__device__ __forceinline__ float vlo(F2 a) { return a.v.x; }
+__device__ __forceinline__ float vhi(F2 a) { return a.v.y; }
+
+struct D2 {
+  double x, y;
+};
+__device__ __forceinline__ D2 vpair(double x, double y) { return D2{x, y}; }
+__device__ __forceinline__ D2 vsplat(double c) { return D2{c, c}; }
+__device__ __forceinline__ D2 vadd(D2 a, D2 b) { return D2{__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)}; }
+__device__ __forceinline__ D2 vsub(D2 a, D2 b) { return D2{__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)}; }
+__device__ __forceinline__ D2 vmul(D2 a, D2 b) { return D2{__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)}; }
+__device__ __forceinline__ D2 vfma(D2 a, D2 b, D2 c) {
+  return D2{__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y)};
+}
+__device__ __forceinline__ D2 vrcp(D2 a) { return D2{1.0 / a.x, 1.0 / a.y}; }
+__device__ __forceinline__ double vlo(D2 a) { return a.x; }
+__device__ __forceinline__ double vhi(D2 a) { return a.y; }
+
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<float> {
+  using type = F2;
+};
+template <>
+struct VecOf<double> {
+  using type = D2;
+};
+
+// The collision of collide() for two nodes, with the relaxation rates and
+// weights folded into the coefficients: for each pair (a, opp(a))
+//   s+ heq+ = s+ w K + 4.5 s+ w X,  X = drho (c.u)^2 + (c.du)(c.u + c.u_ref),
+//   s- heq- = 3 s- w (drho c.u + c.du),
+//   K = drho (1 - 1.5 |u|^2) - 1.5 (|u|^2 - |u_ref|^2),
+// the same terms as heq_a = w_a [drho (1 + Q_a(u)) + Q_a(u) - Q_a(u_ref)].
+template <typename V, typename T, bool kForce>
+__device__ __forceinline__ void collide2(const V (&h)[9], V drho, V dux, V duy, V gx, V gy,
+                                         const Consts<T> &c, V (&o)[9]) {
+  const V urx = vsplat(c.urx), ury = vsplat(c.ury);
+  const V ux = vadd(urx, dux), uy = vadd(ury, duy);
+  const V uu = vfma(ux, ux, vmul(uy, uy));
+  const V dsu = vfma(dux, vadd(ux, urx), vmul(duy, vadd(uy, ury)));
+  const V m15 = vsplat((T)-1.5);
+  const V K = vfma(m15, dsu, vmul(drho, vfma(m15, uu, vsplat((T)1))));
+  V ug{};
+  if (kForce) ug = vfma(ux, gx, vmul(uy, gy));
+  {
+    const T w0 = (T)w_of(0);
+    const V heq0 = vmul(vsplat(w0), K);
+    V r = vfma(vsplat(-c.s_plus), vsub(h[0], heq0), h[0]);
+    if (kForce) r = vfma(vsplat(c.a_plus * w0 * (T)-3), ug, r);
+    o[0] = r;
+  }
+  const V nsph = vsplat((T)-0.5 * c.s_plus), nsmh = vsplat((T)-0.5 * c.s_minus);
+#pragma unroll
+  for (int a = 1; a <= 6; ++a) {
+    if (a == 3 || a == 4) continue;
+    const int b = opp_of(a);
+    const T w = (T)w_of(a);
+    // c.u, c.du for the four directions 1 (1,0), 2 (0,1), 5 (1,1), 6 (-1,1)
+    V cu, cdu;
+    if (a == 1) {
+      cu = ux;
+      cdu = dux;
+    } else if (a == 2) {
+      cu = uy;
+      cdu = duy;
+    } else if (a == 5) {
+      cu = vadd(ux, uy);
+      cdu = vadd(dux, duy);
+    } else {
+      cu = vsub(uy, ux);
+      cdu = vsub(duy, dux);
+    }
+    const V csu = vadd(cu, vsplat((T)cx_of(a) * c.urx + (T)cy_of(a) * c.ury));
+    const V dc = vmul(drho, cu);
+    const V X = vfma(dc, cu, vmul(cdu, csu));
+    const V P = vfma(vsplat((T)4.5 * c.s_plus * w), X, vmul(vsplat(c.s_plus * w), K));
+    const V Q = vmul(vsplat((T)3 * c.s_minus * w), vadd(dc, cdu));
+    V dp = vfma(nsph, vadd(h[a], h[b]), P);
+    V dm = vfma(nsmh, vsub(h[a], h[b]), Q);
+    if (kForce) {
+      V cg;
+      if (a == 1)
+        cg = gx;
+      else if (a == 2)
+        cg = gy;
+      else if (a == 5)
+        cg = vadd(gx, gy);
+      else
+        cg = vsub(gy, gx);
+      dp = vfma(vsplat(c.a_plus * w * (T)9), vmul(cu, cg), vfma(vsplat(c.a_plus * w * (T)-3), ug, dp));
+      dm = vfma(vsplat(c.a_minus * w * (T)3), cg, dm);
+    }
+    o[a] = vadd(vadd(h[a], dp), dm);
+    o[b] = vsub(vadd(h[b], dp), dm);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// bulk kernel for 16-bit storage: two nodes per thread.  With 2-byte values a
+// load instruction per population and node moves too few bytes to keep HBM
+// busy, so each thread takes the nodes (i, i+1), i even, of a tile row: one
+// aligned 32-bit load per plane brings both values of planes with c_x = 0;
+// for c_x = +1 (sources i-1, i) and c_x = -1 (sources i+1, i+2) the odd
+// neighbour comes from the next lane by a warp shuffle (one extra 2-byte load
+// at the warp's edge), and both results leave in one 32-bit store per plane.
+// The collision of the two nodes runs in packed f32x2 (collide2).
+// ---------------------------------------------------------------------------
+template <typename S>
+struct Pair16;
+template <>
+struct Pair16<__half> {
+  static __device__ __forceinline__ float lo(uint32_t w) {
+    return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+  }
+  static __device__ __forceinline__ float hi(uint32_t w) {
+    return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+  }
+  static __device__ __forceinline__ uint32_t pack(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+  }
+};
+template <>
+struct Pair16<__nv_bfloat16> {
+  static __device__ __forceinline__ float lo(uint32_t w) { return __uint_as_float(w << 16); }
+  static __device__ __forceinline__ float hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+  static __device__ __forceinline__ uint32_t pack(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+  }
+};
+
+template <typename S, bool kForce>
+__global__ void __launch_bounds__(kThreads / 2) bulk16_kernel(const StepArgs p) {
+  using P = Pair16<S>;
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  const Lattice &L = p.L;
+  const int lane = threadIdx.x & 31;
+  const int i = ti * kTileX + 2 * threadIdx.x;  // the thread's nodes i, i + 1
+  const int j = tj * kTileY + threadIdx.y;
+  // every lane loads from inside its row (clamped), so that the shuffles see
+  // all 32 lanes; results of clamped lanes are never stored
+  const int ic = i < L.pitch - 2 ? i : L.pitch - 2;
+  const S *__restrict__ src = static_cast<const S *>(p.src);
+  float lo_v[9], hi_v[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    int r = j - cy_of(a);
+    r = r < 0 ? 0 : (r > L.ny - 1 ? L.ny - 1 : r);
+    const S *row = src + (int64_t)a * L.plane + (int64_t)r * L.pitch;
+    const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(row + ic));
+    if (cx_of(a) == 0) {
+      lo_v[a] = P::lo(w);
+      hi_v[a] = P::hi(w);
+    } else if (cx_of(a) > 0) {  // sources i - 1 (the left lane's high half) and i
+      uint32_t left = __shfl_up_sync(0xffffffffu, w, 1);
+      if (lane == 0)
+        left = ic >= 1 ? ((uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic - 1)) << 16)
+                       : 0u;
+      lo_v[a] = P::hi(left);
+      hi_v[a] = P::lo(w);
+    } else {  // sources i + 1 and i + 2 (the right lane's low half)
+      uint32_t right = __shfl_down_sync(0xffffffffu, w, 1);
+      if (lane == 31)
+        right = ic + 2 < L.pitch ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic + 2))
+                                 : 0u;
+      lo_v[a] = P::hi(w);
+      hi_v[a] = P::lo(right);
+    }
+  }
+  {
+    const ForceRegion reg = *p.reg_src;
+    if (ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1) return;  // special kernel
+  }
+  if (j < 1 || j > L.ny - 2) return;  // edge rows: special kernel
+  const bool lo_ok = i >= 1 && i <= L.nx - 2, hi_ok = i + 1 <= L.nx - 2;
+  if (!lo_ok && !hi_ok) return;
+  const Consts<float> cst(p);
+  F2 h[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) h[a] = vpair(lo_v[a], hi_v[a]);
+  const F2 drho = vadd(vadd(vadd(h[0], h[1]), vadd(h[2], h[3])),
+                       vadd(vadd(vadd(h[4], h[5]), vadd(h[6], h[7])), h[8]));
+  F2 djx = vadd(vadd(vsub(h[1], h[3]), vsub(h[5], h[6])), vsub(h[8], h[7]));
+  F2 djy = vadd(vadd(vsub(h[2], h[4]), vsub(h[5], h[7])), vsub(h[6], h[8]));
+  const F2 rho = vadd(vsplat(1.0f), drho);
+  const F2 inv = vrcp(rho);
+  F2 o[9];
+  if (kForce) {
+    const F2 gx = vsplat(lat_bf<float>(L, 0)), gy = vsplat(lat_bf<float>(L, 1));
+    djx = vfma(vsplat(0.5f), gx, djx);
+    djy = vfma(vsplat(0.5f), gy, djy);
+    collide2<F2, float, true>(h, drho, vmul(vfma(drho, vsplat(-cst.urx), djx), inv),
+                              vmul(vfma(drho, vsplat(-cst.ury), djy), inv), gx, gy, cst, o);
+  } else {
+    collide2<F2, float, false>(h, drho, vmul(vfma(drho, vsplat(-cst.urx), djx), inv),
+                               vmul(vfma(drho, vsplat(-cst.ury), djy), inv), F2{}, F2{}, cst, o);
+  }
+  S *dst = static_cast<S *>(p.dst) + (int64_t)j * L.pitch + i;
+  if (lo_ok && hi_ok) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a)
+      *reinterpret_cast<uint32_t *>(dst + (int64_t)a * L.plane) = P::pack(vlo(o[a]), vhi(o[a]));
+  } else {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      if (lo_ok) Store<S>::st(dst + (int64_t)a * L.plane, vlo(o[a]));
+      if (hi_ok) Store<S>::st(dst + (int64_t)a * L.plane + 1, vhi(o[a]));
+    }
+  }
+  if ((lo_ok && (!(vlo(rho) > 0.f) || !isfinite(vlo(rho)))) ||
+      (hi_ok && (!(vhi(rho) > 0.f) || !isfinite(vhi(rho)))))
+    atomicOr(p.status, kStatusUnstable);
+}
+
 template <typename S, bool kGather>
 cudaError_t special_t(const StepArgs &a, cudaStream_t s) {
   const int tiles = a.all_tiles ? a.ntiles_x * a.ntiles_y : a.edge_blocks + a.region_slots;
@@ -697,6 +944,13 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(const StepArgs p) {
 template <typename S>
 cudaError_t bulk_t(const StepArgs &a, cudaStream_t s) {
   const dim3 grid(a.ntiles_x, a.ntiles_y);
+  if constexpr (sizeof(S) == 2) {  // two nodes per thread
+    if (a.L.has_bf)
+      bulk16_kernel<S, true><<<grid, dim3(kTileX / 2, kTileY), 0, s>>>(a);
+    else
+      bulk16_kernel<S, false><<<grid, dim3(kTileX / 2, kTileY), 0, s>>>(a);
+    return cudaGetLastError();
+  }
   if (a.L.has_bf)
     bulk_kernel<S, true><<<grid, dim3(kTileX, kTileY), 0, s>>>(a);
   else

@@ -94,7 +94,7 @@ def test_streaming_moves_are_bit_exact(bc, dtype, shape):
 
 
 @pytest.mark.parametrize("body", ["none", "disk"])
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16", "bf16"])
 def test_one_step_across_tile_columns(dtype, body):
     """One full time step (pull, moments, penalization, collision) from a
     random post-collision state on a lattice three tiles wide (128, 128 and a
@@ -114,7 +114,10 @@ def test_one_step_across_tile_columns(dtype, body):
     cfg, ob, chi, _, _ = oracle_setup(w)
     f1 = o.stream(cfg, stored, stored)
     ref = o.stream(cfg, o.collide(cfg, ob, chi, f1), f1)
-    bound = 1e-13 if dtype == "f64" else 2e-6
+    # FP64 / FP32 arithmetic; the 16-bit forms round each stored result to
+    # half a unit in the last place of its offset f - w, below 0.5 in
+    # magnitude here: 2^-13 (FP16) and 2^-10 (BF16)
+    bound = {"f64": 1e-13, "f32": 2e-6, "f16": 2.0 ** -13 + 1e-6, "bf16": 2.0 ** -10 + 1e-6}[dtype]
     err = np.abs(got - ref)
     bad = np.argwhere(err.max(axis=0) > bound)
     assert err.max() <= bound, (err.max(), bad[:8])
@@ -336,7 +339,12 @@ def test_16bit_storage_errors(dtype, key, offsets):
     """Offsets stored in FP16 / BF16 with an FP32 collide, either from the
     free-stream equilibrium (u_ref = u_in) or from the lattice weights (f - w):
     errors against the FP64 oracle after 1000 steps stay within bounds set by
-    the storage precision (2^-11 and 2^-8 relative on the offsets)."""
+    the storage precision (2^-11 and 2^-8 relative on the offsets).  The
+    bounds are envelopes: about twice the largest error seen over two
+    orderings of the same FP32 collision arithmetic (one node per thread with
+    compiler-contracted FMAs, two nodes per thread in packed f32x2), since the
+    rounding of each stored value to 16 bits turns any change in the last bits
+    of the collision into a different trajectory."""
     u_ref = (0.05, 0.0) if offsets == "free-stream" else (0.0, 0.0)
     w = FP32_CASES[key]().with_(dtype=dtype, u_ref=u_ref)
     lat = lattice(w)
@@ -348,7 +356,7 @@ def test_16bit_storage_errors(dtype, key, offsets):
             for g, ref in ((fm, r["mh"][-1]), (fs, r["sh"][-1]))]
     print(dtype, key, offsets, "field errors", errs, "force errors", ferr)
     bounds = {("f16", "free-stream"): (2e-3, 6e-3), ("f16", "weights"): (6e-3, 6e-3),
-              ("bf16", "free-stream"): (3e-2, 5e-2), ("bf16", "weights"): (8e-2, 0.3)}
+              ("bf16", "free-stream"): (3e-2, 0.1), ("bf16", "weights"): (8e-2, 0.3)}
     u_bound, f_bound = bounds[(dtype, offsets)]
     assert max(errs[1:]) <= u_bound and max(ferr) <= f_bound
 
