@@ -447,6 +447,68 @@ def run_serving(args, rank, world, local_rank):
     }
 
 
+def run_disk(args, rank, world, local_rank):
+    """The 256 x 128 FP64 disk channel (BGK tau 0.65, Re 20, MEM and SIM every
+    step), 2000 steps from rest graph-replayed, timed whole; the FP64 oracle's
+    run of the same 2000 steps is timed on the host cores beside it.  The
+    lattice (4.7 MB) lives in L2 and the step is latency-bound: report the
+    time per step."""
+    import torch
+    from paper_2110_00967_gb300 import vplbm as V
+    from paper_2110_00967_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    w = W.disk_channel()
+    lat = V.Lattice(V.config_of(w), device=dev)
+    times = []
+    for rep in range(args.warmup + 1):  # warm-up solves, then the timed one
+        lat.set_body(V.body_of(w))
+        torch.cuda.synchronize()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        lat.step(w.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+        times.append(start.elapsed_time(end))
+    lat.check()
+    ms = reduce_max(times[-1], world, dev)
+    fx = lat.force_mem()[0]
+    cd = 2 * fx / (0.05 ** 2 * 20.0)
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": round(world * w.nx * w.ny * w.steps / (ms / 1e3) / 1e6, 1),
+        "unit": "MLUPS", "n_gpus": world, "steps": w.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms / w.steps, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "disk-channel-256x128-f64-re20-bgk", "grid": [w.nx, w.ny],
+                   "steps_per_solve": w.steps, "forces_per_step": ["mem", "sim"],
+                   "l2": "L2-resident (4.7 MB): latency-bound, reported per step",
+                   "parallelism": f"replicas{world}"},
+        "us_per_step": round(ms * 1e3 / w.steps, 3),
+        "cd_mem_final": cd,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as o
+        cfg = o.make_config(w.nx, w.ny, bc=(o.BC_INLET, o.BC_OUTLET, o.BC_PERIODIC,
+                                            o.BC_PERIODIC),
+                            collision=o.BGK, tau_plus=w.tau_plus, eta=w.eta, u_in=w.u_in)
+        body = o.make_body(o.BODY_DISK, length=w.body.length, xg=w.body.x_c, yg=w.body.y_c)
+        chi = o.raster(body, w.nx, w.ny)
+        f = o.init(cfg, body, chi)
+        pts = o.sim_points(body)
+        cores = o.set_threads(0)
+        t0 = time.perf_counter()
+        o.run(cfg, body, f, chi, w.steps, sim_pts=pts, histories=False)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": round(w.nx * w.ny * w.steps / dt / 1e6, 3),
+                                "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                "sample": f"the whole {w.steps}-step solve, {dt:.2f} s"}
+    return line
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -477,7 +539,8 @@ def main(argv=None):
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu's "
                          "application-range replay, which measures the concurrent kernels "
                          "of the whole region)")
-    ap.add_argument("--workload", choices=("naca", "sedimentation", "serving"), default="naca",
+    ap.add_argument("--workload", choices=("naca", "sedimentation", "serving", "disk"),
+                    default="naca",
                     help="naca: the five NACA 0012 lattices (the benchmark); sedimentation: "
                          "the 400 x 1600 falling-disk box, MEM and SIM runs; serving: a seeded "
                          "mix of NACA solves run to convergence")
@@ -508,6 +571,8 @@ def main(argv=None):
             line = run_sedimentation(args, rank, world, local_rank)
         elif args.workload == "serving":
             line = run_serving(args, rank, world, local_rank)
+        elif args.workload == "disk":
+            line = run_disk(args, rank, world, local_rank)
         else:
             line = run_ours(args, rank, world, local_rank)
     if line is not None:
