@@ -509,6 +509,72 @@ def run_disk(args, rank, world, local_rank):
     return line
 
 
+def run_naca_paper(args, rank, world, local_rank):
+    """The paper's own NACA 0012 case (C = 278, U0 = 0.0599, tau 0.55, 3614 x
+    1946 FP32) at the angles 0, 4, ..., 28 degrees as one batch; reports the
+    MLUPS of the timed steps and the Cd/Cl means over them (MEM and SIM)."""
+    import torch
+    from paper_2110_00967_gb300 import vplbm as V
+    from paper_2110_00967_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    works = [W.naca_paper(a, dtype=args.dtype) for a in W.PAPER_ANGLES]
+    lats = [V.Lattice(V.config_of(w), device=dev) for w in works]
+    for w, lat in zip(works, lats):
+        lat.set_body(V.body_of(w))
+    batch = V.Batch(lats, stream=stream)
+    batch.step(args.warmup)
+    for lat in lats:
+        lat.reset_sums()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = batch.launches
+    barrier(world)
+    torch.cuda.synchronize()
+    start.record(stream)
+    batch.step(args.steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    elapsed_ms = reduce_max(start.elapsed_time(end), world, dev)
+    q = 0.5 * 0.0599 ** 2 * 278.0
+    coeffs = {}
+    for w, lat in zip(works, lats):
+        lat.check()
+        sums, n = lat.sums()
+        coeffs[f"{w.body.angle_deg:g}"] = {
+            "cd_mem": sums[0] / n[0] / q, "cl_mem": sums[1] / n[0] / q,
+            "cd_sim": sums[3] / n[1] / q, "cl_sim": sums[4] / n[1] / q}
+    nodes = works[0].nx * works[0].ny * len(lats)
+    bpl = BYTES_PER_LUP[args.dtype]
+    lattice_step_ms = elapsed_ms / (args.steps * len(lats))
+    achieved = bpl * nodes / len(lats) / (lattice_step_ms / 1e3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    launches = batch.launches - l0
+    batch.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": round(world * nodes * args.steps / (elapsed_ms / 1e3) / 1e6, 1),
+        "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"naca0012-paper-3614x1946-{args.dtype}-alpha0..28",
+                   "grid": [works[0].nx, works[0].ny], "instances": len(lats), "chord": 278,
+                   "u0": 0.0599, "tau_plus": 0.55, "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "one lattice step, timed over the region",
+                     "kernel_avg_us": round(lattice_step_ms * 1e3, 3), "bytes_per_lup": bpl,
+                     "peak_kind": peak_kind},
+        "means_over_steps": [args.warmup + 1, args.warmup + args.steps],
+        "coefficients": coeffs,
+        "gpu_launches": launches,
+    }
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -539,7 +605,8 @@ def main(argv=None):
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu's "
                          "application-range replay, which measures the concurrent kernels "
                          "of the whole region)")
-    ap.add_argument("--workload", choices=("naca", "sedimentation", "serving", "disk"),
+    ap.add_argument("--workload",
+                    choices=("naca", "sedimentation", "serving", "disk", "naca-paper"),
                     default="naca",
                     help="naca: the five NACA 0012 lattices (the benchmark); sedimentation: "
                          "the 400 x 1600 falling-disk box, MEM and SIM runs; serving: a seeded "
@@ -573,6 +640,8 @@ def main(argv=None):
             line = run_serving(args, rank, world, local_rank)
         elif args.workload == "disk":
             line = run_disk(args, rank, world, local_rank)
+        elif args.workload == "naca-paper":
+            line = run_naca_paper(args, rank, world, local_rank)
         else:
             line = run_ours(args, rank, world, local_rank)
     if line is not None:

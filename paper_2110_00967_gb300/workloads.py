@@ -79,7 +79,8 @@ def disk_channel() -> Workload:
 
 
 def naca(alpha_deg: float = 0.0, dtype: str = "f32", nx: int = 2048, ny: int = 1024,
-         chord: float | None = None, steps: int = 200_000, u_ref=None) -> Workload:
+         chord: float | None = None, steps: int = 200_000, u_ref=None, u0: float = 0.05,
+         tau_plus: float = 0.53) -> Workload:
     """NACA 0012 at Re 1000 on the chord (C = 200 on 2048 x 1024): leading edge
     at x = 4C, chord line half-way between the two middle rows, rotation about
     the quarter chord (nose up for alpha > 0), inlet u = 0.05, convective
@@ -89,17 +90,32 @@ def naca(alpha_deg: float = 0.0, dtype: str = "f32", nx: int = 2048, ny: int = 1
     (u_ref = u_in) unless u_ref is given; (0, 0) gives the f - w offsets."""
     c = chord if chord is not None else nx * 200.0 / 2048.0
     if u_ref is None:
-        u_ref = (0.0, 0.0) if dtype == "f64" else (0.05, 0.0)
+        u_ref = (0.0, 0.0) if dtype == "f64" else (u0, 0.0)
     return Workload(
         name=f"naca0012-{nx}x{ny}-a{alpha_deg:g}-{dtype}", nx=nx, ny=ny, dtype=dtype,
-        collision="trt", tau_plus=0.53,
-        u_in=(0.05, 0.0), bc=(INLET, OUTLET, SYMMETRY, SYMMETRY),
+        collision="trt", tau_plus=tau_plus,
+        u_in=(u0, 0.0), bc=(INLET, OUTLET, SYMMETRY, SYMMETRY),
         body=Body("naca", length=c, thickness=0.12, x_c=4.0 * c + 0.25 * c,
                   y_c=(ny - 1) / 2.0, angle_deg=alpha_deg),
         steps=steps, u_ref=tuple(u_ref))
 
 
 NACA_ANGLES = (0.0, 5.0, 10.0, 15.0, 20.0)
+
+
+def naca_paper(alpha_deg: float = 0.0, dtype: str = "f32", steps: int = 200_000) -> Workload:
+    """The paper's own NACA 0012 case (Sec. 3.1): chord C = 278, U0 = 0.0599,
+    tau = 0.55 (Re = U0 C / nu = 999), the leading edge 4C from the inlet and
+    9C to the outlet (13C = 3614 columns), 7C high (1946 rows) with the chord
+    line 3.5C from the bottom wall (mid-height, the wall half-way below row 0),
+    rotation about the quarter chord, half-way bounce-back inlet, convective
+    outlet, symmetry top and bottom, TRT Lambda = 1/6, 849 SIM points."""
+    c = 278.0
+    return naca(alpha_deg, dtype=dtype, nx=int(13 * c), ny=int(7 * c), chord=c, steps=steps,
+                u0=0.0599, tau_plus=0.55)
+
+
+PAPER_ANGLES = (0.0, 4.0, 8.0, 12.0, 16.0, 20.0, 24.0, 28.0)
 
 
 def sedimentation(estimator: str = "mem", steps: int = 100_000) -> Workload:

@@ -384,6 +384,29 @@ def test_naca_full_size_sampled():
         assert np.abs(g[:2] - r[:2]).max() <= 1e-3 * np.abs(r[:2]).max()
 
 
+def test_naca_paper_geometry_sampled():
+    """The paper's own NACA 0012 case (C = 278, U0 = 0.0599, tau 0.55, 3614 x 1946)
+    at 26 degrees, FP32: after 40 steps, 2000 sampled nodes and both forces agree
+    with the FP64 oracle run at full size."""
+    w = W.naca_paper(26.0, dtype="f32", steps=40)
+    lat = lattice(w)
+    lat.step(w.steps)
+    cfg, body, chi, f, pts = oracle_setup(w)
+    assert len(pts) == 849
+    mh, sh, _, bad = o.run(cfg, body, f, chi, w.steps, sim_pts=pts)
+    assert bad == 0
+    assert np.array_equal(lat.get_mask(), chi)
+    rng = np.random.default_rng(6)
+    idx = rng.integers(0, w.nx * w.ny, 2000)
+    rho, ux, uy = lat.get_fields()
+    r0, x0, y0 = o.fields(cfg, body, chi, f)
+    for g, r, sub in ((rho, r0, 1.0), (ux, x0, 0.0), (uy, y0, 0.0)):
+        g, r = g.ravel()[idx] - sub, r.ravel()[idx] - sub
+        assert np.abs(g - r).max() <= 1e-5 * np.abs(r).max()
+    for g, r in ((lat.force_mem(), mh[-1]), (lat.force_sim(), sh[-1])):
+        assert np.abs(g[:2] - r[:2]).max() <= 1e-3 * np.abs(r[:2]).max()
+
+
 def test_history_ring_wraps():
     """A short history ring that has wrapped returns the same last rows as a long one."""
     w = W.naca(5.0, dtype="f32", nx=256, ny=128)
