@@ -113,6 +113,7 @@ def lib():
         L.orc_fields.argtypes = [P(Config), P(Body), u8p, dp, dp, dp, dp]
         L.orc_stream.argtypes = [P(Config), dp, dp, dp]
         L.orc_mem.argtypes = [P(Config), P(Body), u8p, dp, dp]
+        L.orc_angot.argtypes = [P(Config), P(Body), u8p, dp, dp]
         L.orc_sim_points.argtypes = [P(Body), C.c_int32, dp]
         L.orc_sim_points.restype = C.c_int
         L.orc_sim_direction.argtypes = [C.c_double, C.c_double]
@@ -229,6 +230,15 @@ def stream(cfg: Config, ft, f_prev):
 def mem(cfg: Config, body: Body, chi, ft):
     out = np.zeros(3)
     lib().orc_mem(C.byref(cfg), C.byref(body), _u8p(chi), _dp(np.ascontiguousarray(ft)), _dp(out))
+    return out
+
+
+def angot(cfg: Config, body: Body, chi, f):
+    """Volume-integral force (F_x, F_y, T) of Eq. Angotforce on the pre-collision
+    field f (reading R19 of the C file)."""
+    out = np.zeros(3)
+    lib().orc_angot(C.byref(cfg), C.byref(body), _u8p(chi), _dp(np.ascontiguousarray(f)),
+                    _dp(out))
     return out
 
 

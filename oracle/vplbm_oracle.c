@@ -38,6 +38,10 @@
  *      over both candidates (keeps mirror-symmetric bodies symmetric).
  *   R7 the tau in the SIM stress is tau+.
  *  R10 convective outlet velocity U_c = |u_in|;  R11 inlet wall density 1.
+ *  R19 the volume-integral force of Eq. Angotforce is the penalization
+ *      force reversed, sum over solid nodes of rho (chi/eta)(u - u_s) (the
+ *      printed formula has lost the 1/eta and writes the limit as eta to
+ *      infinity); the paper reports that it fails, it is a diagnostic.
  */
 #include <math.h>
 #include <stdint.h>
@@ -442,6 +446,34 @@ void orc_mem(const orc_config *cfg, const orc_body *b, const uint8_t *chi, const
   out[0] = fx;
   out[1] = fy;
   out[2] = tq;
+}
+
+/* ---- volume-integral force (Eq. Angotforce, Sec. 2.3) ----------------------
+ * The force the penalization exerts on the fluid, reversed: over the solid
+ * nodes, F = -sum G_pen = sum rho (chi/eta)(u - u_s), with u the penalized
+ * velocity of Eq. updatestepm and G_pen the penalization part of the force
+ * density (reading R19: the printed formula has lost its 1/eta and its limit
+ * is eta -> 0).  Torque about the body reference point.  Evaluated on the
+ * pre-collision field of a step, like SIM; summed j-major, then i. */
+void orc_angot(const orc_config *cfg, const orc_body *b, const uint8_t *chi, const double *f,
+               double *out) {
+  const int nx = cfg->nx, ny = cfg->ny;
+  double F[2] = {0.0, 0.0}, T = 0.0;
+  double fl[Q];
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      if (!chi[(size_t)j * nx + i]) continue;
+      for (int a = 0; a < Q; ++a) fl[a] = f[((size_t)a * ny + j) * nx + i];
+      double rho, u[2], g[2];
+      node_moments(cfg, b, fl, 1, i, j, &rho, u, g);
+      const double fx = -(g[0] - cfg->body_force[0]), fy = -(g[1] - cfg->body_force[1]);
+      F[0] += fx;
+      F[1] += fy;
+      T += (i - b->xg) * fy - (j - b->yg) * fx;
+    }
+  out[0] = F[0];
+  out[1] = F[1];
+  out[2] = T;
 }
 
 /* ---- SIM integration points: a closed polygon, counter-clockwise ---------

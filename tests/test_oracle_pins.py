@@ -578,3 +578,43 @@ def test_naca_zero_angle_lift_vanishes():
     assert np.abs(mh[:, 1]).max() / scale < 1e-10
     assert np.abs(sh[:, 1]).max() / scale < 1e-10
     assert mh[-1, 0] > 0 and sh[-1, 0] > 0
+
+
+# ---------------------------------------------------------------------------
+# volume-integral force (Eq. Angotforce, reading R19)
+# ---------------------------------------------------------------------------
+def test_angot_force_closed_form_for_a_uniform_state():
+    """f = feq(1, u0) on every node around a fixed disk: at a solid node
+    j = u0, u_s = 0, so rho (chi/eta)(u - u_s) = (1/eta) u0 / (1 + 1/(2 eta)),
+    and the force is the solid-node count times 2 u0 / (2 eta + 1); the
+    torque is that node force crossed with the solid nodes' first moment."""
+    nx, ny = 41, 33
+    u0 = np.array([0.03, -0.02])
+    for eta in (1e-6, 0.5, 3.0):
+        cfg = o.make_config(nx, ny, collision=o.TRT, tau_plus=0.6, eta=eta)
+        body = o.make_body(o.BODY_DISK, length=14, xg=20.3, yg=16.1)
+        chi = o.raster(body, nx, ny)
+        f = np.zeros((9, ny, nx))
+        f[:] = o.feq(1.0, *u0)[:, None, None]
+        n = int(chi.sum())
+        per_node = 2.0 * u0 / (2.0 * eta + 1.0)
+        F = o.angot(cfg, body, chi, f)
+        np.testing.assert_allclose(F[:2], n * per_node, rtol=1e-12)
+        jj, ii = np.nonzero(chi)
+        rx, ry = (ii - 20.3).sum(), (jj - 16.1).sum()
+        assert abs(F[2] - (rx * per_node[1] - ry * per_node[0])) <= 1e-12 * n * abs(per_node).max() * 10
+
+
+def test_angot_force_vanishes_at_rest_and_with_the_body_moving_with_the_flow():
+    nx, ny = 40, 30
+    cfg = o.make_config(nx, ny, collision=o.TRT, tau_plus=0.6)
+    body = o.make_body(o.BODY_DISK, length=10, xg=20.2, yg=14.7)
+    chi = o.raster(body, nx, ny)
+    f = o.init(cfg, body, chi)  # rho = 1, u = 0
+    assert np.abs(o.angot(cfg, body, chi, f)).max() == 0.0
+    u0 = (0.04, -0.015)
+    moving = o.make_body(o.BODY_DISK, length=10, xg=20.2, yg=14.7, u=u0)
+    f[:] = o.feq(1.0, *u0)[:, None, None]
+    # round-off of j - rho u_s in each solid node (~1e-17), times about 2 per
+    # node and lever arms of a few nodes
+    assert np.abs(o.angot(cfg, moving, chi, f)).max() < 1e-13
