@@ -79,7 +79,10 @@ typedef enum {
 
 typedef enum { VPLBM_BODY_NONE = 0, VPLBM_BODY_DISK = 1, VPLBM_BODY_NACA4 = 2 } vplbm_body_kind;
 
-typedef enum { VPLBM_MEM = 0, VPLBM_SIM = 1 } vplbm_estimator;
+/* force estimators: momentum exchange (Sec. 2.3.1), stress integration
+ * (Sec. 2.3.2), and the volume integral of Eq. Angotforce (Sec. 2.3), which
+ * the paper reports as failing and which only the history read-backs offer */
+typedef enum { VPLBM_MEM = 0, VPLBM_SIM = 1, VPLBM_ANGOT = 2 } vplbm_estimator;
 
 typedef struct {
   int32_t nx, ny;          /* lattice size, each >= 3 */
@@ -165,6 +168,15 @@ vplbm_status vplbm_force_mem(vplbm_ctx *ctx, double F[2], double *T);
  * ESTATE when SIM has not run or a point found no fluid node. */
 vplbm_status vplbm_force_sim(vplbm_ctx *ctx, double F[2], double *T);
 
+/* Volume-integral force of the last step (Eq. Angotforce, Sec. 2.3): the
+ * penalization force density reversed and summed over the solid nodes,
+ * sum rho (chi/eta)(u - u_s) with u the penalized velocity of Eq.
+ * updatestepm (the printed formula has lost its 1/eta), evaluated with the
+ * collision of the step; torque about the body reference point.  Host
+ * outputs; synchronises the stream.  ESTATE before the first step.  A
+ * diagnostic: the paper reports that this estimator fails. */
+vplbm_status vplbm_force_angot(vplbm_ctx *ctx, double F[2], double *T);
+
 /* Queues a copy of the last step's forces into caller host memory without
  * waiting: out[6] = MEM (F_x, F_y, T) then SIM (F_x, F_y, T) (SIM entries are
  * NaN on steps where SIM was not evaluated).  out should be page-locked for
@@ -172,7 +184,7 @@ vplbm_status vplbm_force_sim(vplbm_ctx *ctx, double F[2], double *T);
  * synchronised.  ESTATE before the first step. */
 vplbm_status vplbm_forces_async(vplbm_ctx *ctx, double *out);
 
-/* Last `count` per-step forces of one estimator, oldest first, host output
+/* Last `count` per-step forces of one estimator (MEM, SIM or ANGOT), oldest first, host output
  * out[count][3] = (F_x, F_y, T).  EINVAL when count exceeds the history length
  * or the number of steps taken. */
 vplbm_status vplbm_force_history(vplbm_ctx *ctx, int32_t estimator, int32_t count, double *out);

@@ -66,7 +66,7 @@ Layout make_layout(const vplbm_config &c) {
   const size_t ms = (size_t)effective_max_sim(c);
   l.sim_pts = take(ms * sizeof(SimPoint));
   l.sim_nodes = take(ms * sizeof(int32_t));
-  l.hist = take((size_t)effective_hist(c) * 6 * sizeof(double));
+  l.hist = take((size_t)effective_hist(c) * kHistCols * sizeof(double));
   l.body[0] = take(sizeof(BodyState));
   l.body[1] = take(sizeof(BodyState));
   l.region[0] = take(sizeof(ForceRegion));
@@ -700,9 +700,10 @@ vplbm_status vplbm_step(vplbm_ctx *c, int32_t nsteps) {
   return VPLBM_OK;
 }
 
-static vplbm_status read_hist_entry(vplbm_ctx *c, long long step, double out[6]) {
+// one history row: MEM (F_x, F_y, T), SIM (same), volume integral (same)
+static vplbm_status read_hist_entry(vplbm_ctx *c, long long step, double out[kHistCols]) {
   const int len = effective_hist(c->cfg);
-  VPLBM_CUDA(c, cudaMemcpyAsync(out, c->hist + 6 * (step % len), 6 * sizeof(double),
+  VPLBM_CUDA(c, cudaMemcpyAsync(out, c->hist + kHistCols * (step % len), kHistCols * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->stream));
   return sync(c);
 }
@@ -711,7 +712,7 @@ vplbm_status vplbm_force_mem(vplbm_ctx *c, double F[2], double *T) {
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!F || !T) return fail(c, VPLBM_EINVAL, "NULL output");
   if (c->steps == 0) return fail(c, VPLBM_ESTATE, "no step taken");
-  double e[6];
+  double e[kHistCols];
   if (vplbm_status st = read_hist_entry(c, c->steps - 1, e)) return st;
   int32_t status = 0;
   if (vplbm_status st = read_status(c, &status)) return st;
@@ -728,7 +729,7 @@ vplbm_status vplbm_force_sim(vplbm_ctx *c, double F[2], double *T) {
   if (c->sim_every <= 0 || c->n_sim <= 0 || c->steps == 0) return fail(c, VPLBM_ESTATE, "SIM not evaluated");
   const long long last = (c->steps - 1) / c->sim_every * c->sim_every;
   if (c->steps - 1 - last >= effective_hist(c->cfg)) return fail(c, VPLBM_ESTATE, "SIM entry left the history");
-  double e[6];
+  double e[kHistCols];
   if (vplbm_status st = read_hist_entry(c, last, e)) return st;
   int32_t status = 0;
   if (vplbm_status st = read_status(c, &status)) return st;
@@ -740,12 +741,24 @@ vplbm_status vplbm_force_sim(vplbm_ctx *c, double F[2], double *T) {
   return VPLBM_OK;
 }
 
+vplbm_status vplbm_force_angot(vplbm_ctx *c, double F[2], double *T) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!F || !T) return fail(c, VPLBM_EINVAL, "NULL output");
+  if (c->steps == 0) return fail(c, VPLBM_ESTATE, "no step taken");
+  double e[kHistCols];
+  if (vplbm_status st = read_hist_entry(c, c->steps - 1, e)) return st;
+  F[0] = e[6];
+  F[1] = e[7];
+  *T = e[8];
+  return VPLBM_OK;
+}
+
 vplbm_status vplbm_forces_async(vplbm_ctx *c, double *out) {
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!out) return fail(c, VPLBM_EINVAL, "NULL output");
   if (c->steps == 0) return fail(c, VPLBM_ESTATE, "no step taken");
   const int len = effective_hist(c->cfg);
-  VPLBM_CUDA(c, cudaMemcpyAsync(out, c->hist + 6 * ((c->steps - 1) % len), 6 * sizeof(double),
+  VPLBM_CUDA(c, cudaMemcpyAsync(out, c->hist + kHistCols * ((c->steps - 1) % len), 6 * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->stream));
   return VPLBM_OK;
 }
@@ -755,21 +768,22 @@ vplbm_status vplbm_force_history(vplbm_ctx *c, int32_t estimator, int32_t count,
   const int len = effective_hist(c->cfg);
   if (!out || count < 0 || count > len || count > c->steps)
     return fail(c, VPLBM_EINVAL, "bad history request");
-  if (estimator != VPLBM_MEM && estimator != VPLBM_SIM) return fail(c, VPLBM_EINVAL, "unknown estimator");
+  if (estimator != VPLBM_MEM && estimator != VPLBM_SIM && estimator != VPLBM_ANGOT)
+    return fail(c, VPLBM_EINVAL, "unknown estimator");
   if (count == 0) return VPLBM_OK;
   // the requested rows only: one copy, or two where they wrap around the ring
-  std::vector<double> rows((size_t)count * 6);
+  std::vector<double> rows((size_t)count * kHistCols);
   const int first = (int)((c->steps - count) % len);
   const int n1 = std::min(count, len - first);
-  VPLBM_CUDA(c, cudaMemcpyAsync(rows.data(), c->hist + 6 * (size_t)first, (size_t)n1 * 6 * sizeof(double),
+  VPLBM_CUDA(c, cudaMemcpyAsync(rows.data(), c->hist + kHistCols * (size_t)first, (size_t)n1 * kHistCols * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->stream));
   if (count > n1)
-    VPLBM_CUDA(c, cudaMemcpyAsync(rows.data() + 6 * (size_t)n1, c->hist, (size_t)(count - n1) * 6 * sizeof(double),
+    VPLBM_CUDA(c, cudaMemcpyAsync(rows.data() + kHistCols * (size_t)n1, c->hist, (size_t)(count - n1) * kHistCols * sizeof(double),
                                   cudaMemcpyDeviceToHost, c->stream));
   if (vplbm_status st = sync(c)) return st;
-  const int off = estimator == VPLBM_SIM ? 3 : 0;
+  const int off = estimator == VPLBM_SIM ? 3 : (estimator == VPLBM_ANGOT ? 6 : 0);
   for (int k = 0; k < count; ++k)
-    for (int q = 0; q < 3; ++q) out[3 * k + q] = rows[6 * (size_t)k + off + q];
+    for (int q = 0; q < 3; ++q) out[3 * k + q] = rows[kHistCols * (size_t)k + off + q];
   return VPLBM_OK;
 }
 

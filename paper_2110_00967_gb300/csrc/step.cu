@@ -314,20 +314,21 @@ __device__ void finalize(const StepArgs &p, unsigned long long *acc) {
     const long long w0 = (long long)__ldcg(acc + 2 * tid);
     const long long w1 = (long long)__ldcg(acc + 2 * tid + 1);
     double v = Fix<T>::value(w0, w1);
-    if (tid >= 3) v += p.sim_const[tid - 3];
+    if (tid >= 3 && tid < 6) v += p.sim_const[tid - 3];
     tot[tid] = v;
   } else if (tid == 64) {
     step_s = __ldcg(p.dev_step);
   }
   __syncthreads();
-  if (tid < 6) {
-    const bool have = tid < 3 || do_sim;
-    p.hist[6 * (step_s % p.hist_len) + tid] =
+  if (tid < kHistCols) {
+    // MEM (0-2) and the volume integral (6-8) every step, SIM (3-5) when due
+    const bool have = tid < 3 || tid >= 6 || do_sim;
+    p.hist[kHistCols * (step_s % p.hist_len) + tid] =
         have ? tot[tid] : __longlong_as_double(0x7ff8000000000000LL);
-    if (have) p.sums[tid] += tot[tid];
-  } else if (tid == 6) {
+    if (have && tid < 6) p.sums[tid] += tot[tid];
+  } else if (tid == 16) {
     p.counts[0] += 1;
-  } else if (tid == 7 && do_sim) {
+  } else if (tid == 17 && do_sim) {
     p.counts[1] += 1;
   } else if (tid == 32) {
     *p.dev_step = step_s + 1;
@@ -354,7 +355,7 @@ __device__ void tail(const StepArgs &p, const ForceRegion &reg) {
     const long long w0 = (long long)__ldcg(p.acc + 2 * tid);
     const long long w1 = (long long)__ldcg(p.acc + 2 * tid + 1);
     double v = Fix<T>::value(w0, w1);
-    if (tid >= 3) v += p.sim_const[tid - 3];
+    if (tid >= 3 && tid < 6) v += p.sim_const[tid - 3];
     tot[tid] = v;
   } else if (tid >= 32 && tid < 32 + kBodyWords) {
     reinterpret_cast<unsigned long long *>(&old_b)[tid - 32] =
@@ -363,14 +364,15 @@ __device__ void tail(const StepArgs &p, const ForceRegion &reg) {
     step_s = __ldcg(p.dev_step);
   }
   __syncthreads();
-  if (tid < 6) {
-    const bool have = tid < 3 || do_sim;
-    p.hist[6 * (step_s % p.hist_len) + tid] =
+  if (tid < kHistCols) {
+    // MEM (0-2) and the volume integral (6-8) every step, SIM (3-5) when due
+    const bool have = tid < 3 || tid >= 6 || do_sim;
+    p.hist[kHistCols * (step_s % p.hist_len) + tid] =
         have ? tot[tid] : __longlong_as_double(0x7ff8000000000000LL);
-    if (have) p.sums[tid] += tot[tid];
-  } else if (tid == 6) {
+    if (have && tid < 6) p.sums[tid] += tot[tid];
+  } else if (tid == 16) {
     p.counts[0] += 1;
-  } else if (tid == 7 && do_sim) {
+  } else if (tid == 17 && do_sim) {
     p.counts[1] += 1;
   } else if (tid == 32) {
     new_b = old_b;
@@ -465,7 +467,9 @@ __device__ __forceinline__ void collide(const T (&h)[9], T drho, T dux, T duy, T
 template <typename T>
 __device__ __forceinline__ bool update_node(const T (&h)[9], uint8_t m, int i, int j,
                                             const Lattice &L, const BodyState *body,
-                                            const Consts<T> &cst, T (&o)[9]) {
+                                            const Consts<T> &cst, T (&o)[9], T &pen_x,
+                                            T &pen_y) {
+  pen_x = pen_y = (T)0;  // the penalization part of G (solid nodes only)
   const T drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
   const T rho = (T)1 + drho;
   // j - u_ref (the offsets' first moment; sum_a c_a E_a = u_ref)
@@ -486,8 +490,10 @@ __device__ __forceinline__ bool update_node(const T (&h)[9], uint8_t m, int i, i
       duy = (djy - drho * cst.ury + k * rho * (usy - cst.ury)) / den;
       // G = -(chi/eta)(j - rho u_s)/(1 + k)
       const T pen = (T)2 * k;
-      gx -= pen * (djx - drho * usx + (cst.urx - usx)) / ((T)1 + k);
-      gy -= pen * (djy - drho * usy + (cst.ury - usy)) / ((T)1 + k);
+      pen_x = -pen * (djx - drho * usx + (cst.urx - usx)) / ((T)1 + k);
+      pen_y = -pen * (djy - drho * usy + (cst.ury - usy)) / ((T)1 + k);
+      gx += pen_x;
+      gy += pen_y;
     } else {
       const T inv = (T)1 / rho;
       dux = (djx - drho * cst.urx) * inv;
@@ -516,7 +522,8 @@ __device__ __forceinline__ void edge_pops(const S *src, const typename Store<S>:
 // an interface node of the force region.
 template <typename S, bool kGather>
 __device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bool in_reg,
-                                             FixAcc<typename Store<S>::T> &acc) {
+                                             FixAcc<typename Store<S>::T> &acc,
+                                             FixAcc<typename Store<S>::T> &vol) {
   using T = typename Store<S>::T;
   const Lattice &L = p.L;
   const S *__restrict__ src = static_cast<const S *>(p.src);
@@ -539,11 +546,20 @@ __device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bo
     pd[2 * L.ny + j] = h[7];
   }
   const uint8_t m = p.chi[node];
-  T o[9];
-  const bool bad = update_node<T>(h, m, i, j, L, p.body_src, Consts<T>(p), o);
+  T o[9], pen_x, pen_y;
+  const bool bad = update_node<T>(h, m, i, j, L, p.body_src, Consts<T>(p), o, pen_x, pen_y);
 #pragma unroll
   for (int a = 0; a < 9; ++a) Store<S>::st(dst + (int64_t)a * L.plane + node, o[a]);
   if (in_reg && (m & kInterface)) mem_terms<T>(p, o, i, j, m, acc);
+  if (in_reg && (m & kSolid)) {
+    // volume integral (Eq. Angotforce, reading R19): the penalization force
+    // on the fluid, reversed, and its moment about the reference point
+    const BodyRef<T> b(*p.body_src);
+    const T fx = -pen_x, fy = -pen_y;
+    vol.add(0, fx);
+    vol.add(1, fy);
+    vol.add(2, ((T)i - b.xg) * fy - ((T)j - b.yg) * fx);
+  }
   return bad;
 }
 
@@ -587,8 +603,8 @@ __global__ void __launch_bounds__(kThreads) special_kernel(const StepArgs p) {
       const int ti = i / kTileX, tj = j / kTileY;
       const bool in_reg = ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1;
       if (!in_reg) {
-        FixAcc<T> unused;
-        bad = special_node<S, kGather>(p, i, j, false, unused);
+        FixAcc<T> unused, unused_vol;
+        bad = special_node<S, kGather>(p, i, j, false, unused, unused_vol);
       }
     }
     if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(p.status, kStatusUnstable);
@@ -611,11 +627,12 @@ __global__ void __launch_bounds__(kThreads) special_kernel(const StepArgs p) {
     const int i = ti * kTileX + threadIdx.x;
     const int j = tj * kTileY + threadIdx.y;
     bool bad = false;
-    FixAcc<T> acc;
-    if (i < L.nx && j < L.ny) bad = special_node<S, kGather>(p, i, j, in_reg, acc);
+    FixAcc<T> acc, vol;
+    if (i < L.nx && j < L.ny) bad = special_node<S, kGather>(p, i, j, in_reg, acc, vol);
     if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(p.status, kStatusUnstable);
     if (!in_reg) return;  // uniform over the block
     warp_add(acc, p.acc, 0);
+    warp_add(vol, p.acc, 6);
   }
 
   if (p.defer) return;  // a later launch finalizes this step's sums

@@ -210,7 +210,9 @@ struct Fix<float> {
   }
 };
 // accumulator words: (MEM Fx, Fy, T, SIM Fx, Fy, T) x two words
-constexpr int kAccSlots = 6;
+// fixed-point sum slots: MEM F_x, F_y, T; SIM F_x, F_y, T; volume integral F_x, F_y, T
+constexpr int kAccSlots = 9;
+constexpr int kHistCols = 9;  // one history row per step: the same nine values
 constexpr int kAccWords = 2 * kAccSlots;
 
 // ---------------------------------------------------------------------------

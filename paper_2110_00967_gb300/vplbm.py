@@ -21,7 +21,7 @@ BGK, TRT = 0, 1
 FORCING_PAPER, FORCING_SPLIT = 0, 1
 PERIODIC, INLET_BB, OUTLET_CONVECTIVE, SYMMETRY, NOSLIP_BB = range(5)
 BODY_NONE, BODY_DISK, BODY_NACA4 = range(3)
-MEM, SIM = 0, 1
+MEM, SIM, ANGOT = 0, 1, 2
 
 _STATUS = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
            EUNSTABLE: "EUNSTABLE", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
@@ -95,6 +95,7 @@ _SIGS = [
     ("vplbm_step", [_vp, C.c_int32], C.c_int),
     ("vplbm_force_mem", [_vp, _P(C.c_double), _P(C.c_double)], C.c_int),
     ("vplbm_force_sim", [_vp, _P(C.c_double), _P(C.c_double)], C.c_int),
+    ("vplbm_force_angot", [_vp, _P(C.c_double), _P(C.c_double)], C.c_int),
     ("vplbm_forces_async", [_vp, _vp], C.c_int),
     ("vplbm_force_history", [_vp, C.c_int32, C.c_int32, _P(C.c_double)], C.c_int),
     ("vplbm_force_sums", [_vp, _P(C.c_double), _P(C.c_int64)], C.c_int),
@@ -189,6 +190,10 @@ def vplbm_force_mem(ctx):
 
 def vplbm_force_sim(ctx):
     return _force(lib().vplbm_force_sim, ctx)
+
+
+def vplbm_force_angot(ctx):
+    return _force(lib().vplbm_force_angot, ctx)
 
 
 def vplbm_forces_async(ctx, host_ptr: int):
@@ -344,6 +349,9 @@ class Lattice:
 
     def force_sim(self):
         return vplbm_force_sim(self.ctx)
+
+    def force_angot(self):
+        return vplbm_force_angot(self.ctx)
 
     def history(self, estimator: int, count: int):
         return vplbm_force_history(self.ctx, estimator, count)
