@@ -114,6 +114,8 @@ def lib():
         L.orc_stream.argtypes = [P(Config), dp, dp, dp]
         L.orc_mem.argtypes = [P(Config), P(Body), u8p, dp, dp]
         L.orc_angot.argtypes = [P(Config), P(Body), u8p, dp, dp]
+        L.orc_sim_order.argtypes = [P(Config), P(Body), u8p, dp, C.c_int32, dp, C.c_int32, dp, i32p, dp]
+        L.orc_sim_order.restype = C.c_int
         L.orc_sim_points.argtypes = [P(Body), C.c_int32, dp]
         L.orc_sim_points.restype = C.c_int
         L.orc_sim_direction.argtypes = [C.c_double, C.c_double]
@@ -262,6 +264,20 @@ def sim_points(body: Body, n: int | None = None) -> np.ndarray:
 
 def sim_direction(nx, ny) -> int:
     return lib().orc_sim_direction(nx, ny)
+
+
+def sim_order(cfg: Config, body: Body, chi, f, pts, order: int):
+    """SIM with the stress copied (order 0) or extrapolated linearly (order 1)
+    to each point; returns (F_x, F_y, T), sampled nodes, missing count and the
+    per-point stresses (xx, xy, yy)."""
+    out = np.zeros(3)
+    nodes = np.zeros(len(pts), np.int32)
+    sig = np.zeros((len(pts), 3))
+    missing = lib().orc_sim_order(C.byref(cfg), C.byref(body), _u8p(chi),
+                                  _dp(np.ascontiguousarray(f)), len(pts),
+                                  _dp(np.ascontiguousarray(pts)), int(order), _dp(out),
+                                  _i32p(nodes), _dp(sig))
+    return out, nodes, missing, sig
 
 
 def sim(cfg: Config, body: Body, chi, f, pts):

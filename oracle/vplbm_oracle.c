@@ -38,6 +38,9 @@
  *      over both candidates (keeps mirror-symmetric bodies symmetric).
  *   R7 the tau in the SIM stress is tau+.
  *  R10 convective outlet velocity U_c = |u_in|;  R11 inlet wall density 1.
+ *  R20 a first-order SIM variant extrapolates the stress linearly to the
+ *      integration point from the first two fluid nodes along the sampling
+ *      direction (the paper copies it from the first, R6).
  *  R19 the volume-integral force of Eq. Angotforce is the penalization
  *      force reversed, sum over solid nodes of rho (chi/eta)(u - u_s) (the
  *      printed formula has lost the 1/eta and writes the limit as eta to
@@ -589,9 +592,18 @@ static int sim_walk(const orc_config *cfg, const uint8_t *chi, int a, int qi, in
   return 0;
 }
 
-int orc_sim(const orc_config *cfg, const orc_body *b, const uint8_t *chi, const double *f,
-            int32_t n, const double *pts, double *out, int32_t *nodes) {
-  int nx = cfg->nx, missing = 0;
+/* SIM force and torque (Eq. defFf) with the stress of Sec. 2.3.2 sampled at
+ * each integration point either as the paper describes it (order 0, reading
+ * R6: the stress of the first fluid node q met along the lattice direction c
+ * closest to the normal), or extrapolated linearly to the point along that
+ * direction (order 1, reading R20): sigma(x_i) = sigma(q) + t (sigma(q + c) -
+ * sigma(q)) with t = (x_i - q).c / |c|^2, falling back to order 0 where q + c
+ * is solid or outside the lattice.  Tie points average over both nodes.
+ * pt_sigma, when given, receives each point's (xx, xy, yy) stress. */
+int orc_sim_order(const orc_config *cfg, const orc_body *b, const uint8_t *chi, const double *f,
+                  int32_t n, const double *pts, int32_t order, double *out, int32_t *nodes,
+                  double *pt_sigma) {
+  int nx = cfg->nx, ny = cfg->ny, missing = 0;
   double fx = 0.0, fy = 0.0, tq = 0.0;
   for (int p = 0; p < n; ++p) {
     const double *pt = pts + 5 * p;
@@ -613,6 +625,14 @@ int orc_sim(const orc_config *cfg, const orc_body *b, const uint8_t *chi, const 
         double fl[Q], s3[3];
         for (int c = 0; c < Q; ++c) fl[c] = f[idx(cfg, c, qi, qj)];
         orc_stress(cfg, fl, s3);
+        const int ni = qi + CX[a], nj = qj + CY[a];
+        if (order == 1 && ni >= 0 && ni < nx && nj >= 0 && nj < ny && !chi[(size_t)nj * nx + ni]) {
+          double s3n[3];
+          for (int c = 0; c < Q; ++c) fl[c] = f[idx(cfg, c, ni, nj)];
+          orc_stress(cfg, fl, s3n);
+          const double t = ((x - qi) * CX[a] + (y - qj) * CY[a]) / (double)(CX[a] * CX[a] + CY[a] * CY[a]);
+          for (int k = 0; k < 3; ++k) s3[k] += t * (s3n[k] - s3[k]);
+        }
         sig[0] += s3[0];
         sig[1] += s3[1];
         sig[2] += s3[2];
@@ -626,6 +646,11 @@ int orc_sim(const orc_config *cfg, const orc_body *b, const uint8_t *chi, const 
     sig[0] /= cnt;
     sig[1] /= cnt;
     sig[2] /= cnt;
+    if (pt_sigma) {
+      pt_sigma[3 * p] = sig[0];
+      pt_sigma[3 * p + 1] = sig[1];
+      pt_sigma[3 * p + 2] = sig[2];
+    }
     double tx = pt[4] * (sig[0] * pt[2] + sig[1] * pt[3]);
     double ty = pt[4] * (sig[1] * pt[2] + sig[2] * pt[3]);
     fx += tx;
@@ -636,6 +661,11 @@ int orc_sim(const orc_config *cfg, const orc_body *b, const uint8_t *chi, const 
   out[1] = fy;
   out[2] = tq;
   return missing;
+}
+
+int orc_sim(const orc_config *cfg, const orc_body *b, const uint8_t *chi, const double *f,
+            int32_t n, const double *pts, double *out, int32_t *nodes) {
+  return orc_sim_order(cfg, b, chi, f, n, pts, 0, out, nodes, NULL);
 }
 
 /* ---- rigid body, Eqs. dep1 and theta2, explicit trapezoid in time -------- */

@@ -618,3 +618,62 @@ def test_angot_force_vanishes_at_rest_and_with_the_body_moving_with_the_flow():
     # round-off of j - rho u_s in each solid node (~1e-17), times about 2 per
     # node and lever arms of a few nodes
     assert np.abs(o.angot(cfg, moving, chi, f)).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# first-order SIM (reading R20)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("gdir", [(1, 0), (0, 1), (1, 1), (-1, 1)])
+def test_first_order_sim_is_exact_for_a_stress_linear_along_the_ray(gdir):
+    """Fluid at rest with rho = 1 + beta (g.x): sigma = -rho/3 I is linear.
+    For every point whose sampling direction c is parallel to g, the
+    first-order stress equals the exact -rho(x_i)/3 (the field does not vary
+    across the ray), while the zeroth-order copy misses it by the distance
+    from the point to the sampled node."""
+    nx, ny, R, beta = 80, 80, 15.3, 1e-3
+    cfg = o.make_config(nx, ny, collision=o.TRT, tau_plus=0.6)
+    body = o.make_body(o.BODY_DISK, length=2 * R, xg=40.2, yg=39.7)
+    chi = o.raster(body, nx, ny)
+    jj, ii = np.mgrid[0:ny, 0:nx]
+    rho = 1 + beta * (gdir[0] * ii + gdir[1] * jj)
+    f = np.stack([o.feq(1.0, 0.0, 0.0)[a] * rho for a in range(9)])
+    pts = o.sim_points(body)
+    _, _, miss1, sig1 = o.sim_order(cfg, body, chi, f, pts, 1)
+    _, _, miss0, sig0 = o.sim_order(cfg, body, chi, f, pts, 0)
+    assert miss1 == 0 and miss0 == 0
+    cx, cy, _, _ = o.lattice()
+    dirs = np.array([o.sim_direction(p[2], p[3]) for p in pts])
+    sel = np.array([(cx[a], cy[a]) in (gdir, (-gdir[0], -gdir[1])) for a in dirs])
+    assert sel.sum() >= 8
+    x, y = 40.2 + pts[:, 0], 39.7 + pts[:, 1]
+    exact = -(1 + beta * (gdir[0] * x + gdir[1] * y)) / 3.0
+    np.testing.assert_allclose(sig1[sel, 0], exact[sel], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(sig1[sel, 2], exact[sel], rtol=0, atol=1e-15)
+    assert np.abs(sig1[sel, 1]).max() < 1e-15
+    assert np.abs(sig0[sel, 0] - exact[sel]).max() > 1e-5  # the copy is off by O(beta d)
+
+
+def test_first_order_sim_falls_back_to_the_copy_without_a_second_fluid_node():
+    """Points whose second node along the ray is solid or outside use the
+    copy: on a lattice one node wider than the body, first and zeroth order
+    coincide wherever the ray leaves the lattice after one node."""
+    nx, ny = 24, 24
+    cfg = o.make_config(nx, ny, collision=o.TRT, tau_plus=0.6)
+    body = o.make_body(o.BODY_DISK, length=20.0, xg=11.5, yg=11.5)
+    chi = o.raster(body, nx, ny)
+    f = o.init(cfg, body, chi)
+    rng = np.random.default_rng(3)
+    f = f * (1 + 1e-3 * rng.random(f.shape))
+    pts = o.sim_points(body)
+    out0, n0, m0, s0 = o.sim_order(cfg, body, chi, f, pts, 0)
+    out1, n1, m1, s1 = o.sim_order(cfg, body, chi, f, pts, 1)
+    assert m0 == m1 and np.array_equal(n0, n1)
+    cx, cy, _, _ = o.lattice()
+    for k, p in enumerate(pts):
+        if n0[k] < 0:
+            continue
+        a = o.sim_direction(p[2], p[3])
+        qi, qj = n0[k] % nx, n0[k] // nx
+        ni, nj = qi + cx[a], qj + cy[a]
+        if not (0 <= ni < nx and 0 <= nj < ny) or chi[nj, ni]:
+            np.testing.assert_array_equal(s1[k], s0[k])
