@@ -320,11 +320,15 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
-def run_sedimentation(args, rank, world, local_rank):
+def run_sedimentation(args, rank, world, local_rank, paper=False):
     """The sedimentation box (400 x 1600 FP32, disk D = 50, rho_s/rho = 1.03,
-    rigid body driven by MEM in one run and by SIM in the other), released at
-    rest and stepped warmup + steps times; the timed region covers the last
-    `steps` steps of both runs.  Reports the trajectory's end state."""
+    rigid body driven by MEM in one run and by SIM in the other), or with
+    `paper` the paper's own channel (3120 x 208, D = 26, zero-velocity inlet
+    above, free outlet below; the four density ratios, each driven by MEM and
+    by SIM: eight lattices), released at rest and stepped warmup + steps
+    times; the timed region covers the last `steps` steps of every run.
+    Reports the trajectories' end states (and, for the paper's channel, the
+    particle Reynolds numbers beside the paper's terminal values)."""
     import torch
     from paper_2110_00967_gb300 import vplbm as V
     from paper_2110_00967_gb300 import workloads as W
@@ -332,7 +336,10 @@ def run_sedimentation(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    works = [W.sedimentation(e) for e in ("mem", "sim")]
+    if paper:
+        works = [W.sedimentation_paper(r, e) for r in W.RHO_R_PAPER for e in ("mem", "sim")]
+    else:
+        works = [W.sedimentation(e) for e in ("mem", "sim")]
     lats = [V.Lattice(V.config_of(w), device=dev) for w in works]
     for w, lat in zip(works, lats):
         lat.set_body(V.body_of(w))
@@ -360,9 +367,16 @@ def run_sedimentation(args, rank, world, local_rank):
     for w, lat in zip(works, lats):
         lat.check()
         x, y, th, ux, uy, om = lat.get_body()
-        traj[w.body.estimator] = {"x": x, "y": y, "u_x": ux, "u_y": uy, "omega": om,
-                                  "fall": w.body.y_c - y,
-                                  "re_particle": abs(uy) * w.body.length / nu}
+        fall_u = ux if paper else -uy  # the fall runs along +x in the paper's channel
+        rec = {"x": x, "y": y, "u_x": ux, "u_y": uy, "omega": om,
+               "fall": (x - w.body.x_c) if paper else (w.body.y_c - y),
+               "re_particle": abs(fall_u) * w.body.length / nu}
+        if paper:
+            k = W.RHO_R_PAPER.index(w.body.density_ratio)
+            rec["re_paper"] = W.RE_TERMINAL_PAPER[k]
+            traj[f"rho{w.body.density_ratio}-{w.body.estimator}"] = rec
+        else:
+            traj[w.body.estimator] = rec
     bpl = BYTES_PER_LUP["f32"]
     lattice_step_ms = elapsed_ms / (args.steps * len(lats))
     achieved = bpl * nodes / len(lats) / (lattice_step_ms / 1e3) / 1e9
@@ -375,10 +389,14 @@ def run_sedimentation(args, rank, world, local_rank):
         "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed_ms / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "sedimentation-400x1600-f32-disk50-rho1.03-mem,sim",
-                   "grid": [works[0].nx, works[0].ny], "instances": 2, "tau_plus": 0.6,
-                   "gravity": works[0].body.gravity[1], "rigid_update": "fp64 every step",
-                   "parallelism": f"replicas{world}"},
+        "config": {"workload": ("sedimentation-paper-3120x208-f32-disk26-rho1.0015,1.003,1.01,"
+                                "1.03-mem,sim-inlet0-free-outlet" if paper else
+                                "sedimentation-400x1600-f32-disk50-rho1.03-mem,sim"),
+                   "grid": [works[0].nx, works[0].ny], "instances": len(lats), "tau_plus": 0.6,
+                   "gravity": max(abs(g) for g in works[0].body.gravity),
+                   "rigid_update": "fp64 every step", "parallelism": f"replicas{world}",
+                   **({"physical_time_s": (args.warmup + args.steps) * W.sedimentation_paper_dt()}
+                      if paper else {})},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                      "kernel": "one lattice step (bulk + special with rigid update and "
@@ -606,11 +624,15 @@ def main(argv=None):
                          "application-range replay, which measures the concurrent kernels "
                          "of the whole region)")
     ap.add_argument("--workload",
-                    choices=("naca", "sedimentation", "serving", "disk", "naca-paper"),
+                    choices=("naca", "sedimentation", "serving", "disk", "naca-paper",
+                             "sedimentation-paper"),
                     default="naca",
                     help="naca: the five NACA 0012 lattices (the benchmark); sedimentation: "
                          "the 400 x 1600 falling-disk box, MEM and SIM runs; serving: a seeded "
-                         "mix of NACA solves run to convergence")
+                         "mix of NACA solves run to convergence; disk: the FP64 disk channel; "
+                         "naca-paper: the paper's C = 278 NACA grid at its angles; "
+                         "sedimentation-paper: the paper's D = 26 channel, four density "
+                         "ratios, MEM and SIM (about 203,000 steps reach 1 s)")
     ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
     ap.add_argument("--cap", type=int, default=20000, help="serving: step cap per request")
     ap.add_argument("--memory-gb", type=int, default=40, help="serving: device-memory budget")
@@ -634,8 +656,9 @@ def main(argv=None):
     else:
         from __graft_entry__ import build
         build()
-        if args.workload == "sedimentation":
-            line = run_sedimentation(args, rank, world, local_rank)
+        if args.workload in ("sedimentation", "sedimentation-paper"):
+            line = run_sedimentation(args, rank, world, local_rank,
+                                     paper=args.workload == "sedimentation-paper")
         elif args.workload == "serving":
             line = run_serving(args, rank, world, local_rank)
         elif args.workload == "disk":

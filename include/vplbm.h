@@ -66,7 +66,9 @@ typedef enum { VPLBM_FORCING_PAPER = 0, VPLBM_FORCING_SPLIT = 1 } vplbm_forcing;
 
 /* Side conditions (Sec. 3.1 and 3.2).  x sides: PERIODIC (both), INLET_BB
  * (half-way bounce-back from a wall moving at u_in), OUTLET_CONVECTIVE (x_hi
- * only; convective condition with U_c = |u_in|), NOSLIP_BB.  y sides:
+ * only; convective condition with U_c = |u_in|), OUTLET_FREE (x_hi only; the
+ * "free flow" outlet of Sec. 3.2 read as a zero normal gradient: populations
+ * entering the last column copy those of the column before it), NOSLIP_BB.  y sides:
  * PERIODIC (both), SYMMETRY (specular reflection), NOSLIP_BB.  Walls sit half
  * a cell beyond the edge nodes. */
 typedef enum {
@@ -74,7 +76,8 @@ typedef enum {
   VPLBM_INLET_BB = 1,
   VPLBM_OUTLET_CONVECTIVE = 2,
   VPLBM_SYMMETRY = 3,
-  VPLBM_NOSLIP_BB = 4
+  VPLBM_NOSLIP_BB = 4,
+  VPLBM_OUTLET_FREE = 5
 } vplbm_bc;
 
 typedef enum { VPLBM_BODY_NONE = 0, VPLBM_BODY_DISK = 1, VPLBM_BODY_NACA4 = 2 } vplbm_body_kind;
@@ -93,6 +96,9 @@ typedef struct {
   int32_t sim_every;       /* evaluate SIM every k-th step (0: never) */
   int32_t max_sim_points;  /* capacity for SIM points (0: 4096) */
   int32_t history_len;     /* per-step force history ring length (0: 1024) */
+  int32_t sim_order;       /* SIM stress at a point: 0 copied from the first fluid node along
+                              the sampling direction (Sec. 2.3.2); 1 extrapolated linearly
+                              from the first two (not in the paper) */
   double tau_plus;         /* > 1/2; nu = (tau+ - 1/2)/3 (Eq. tauvisco) */
   double lambda_trt;       /* TRT magic parameter Lambda (1/6 in Sec. 2.2) */
   double eta;              /* penalization factor, > 0 (1e-6 in Sec. 3) */

@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BC_PERIODIC, BC_INLET, BC_OUTLET, BC_SYMMETRY, BC_NOSLIP = 0, 1, 2, 3, 4
+BC_PERIODIC, BC_INLET, BC_OUTLET, BC_SYMMETRY, BC_NOSLIP, BC_OUTLET_FREE = 0, 1, 2, 3, 4, 5
 BGK, TRT = 0, 1
 FORCING_PAPER, FORCING_SPLIT = 0, 1
 BODY_NONE, BODY_DISK, BODY_NACA = 0, 1, 2

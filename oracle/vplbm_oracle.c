@@ -41,6 +41,9 @@
  *  R20 a first-order SIM variant extrapolates the stress linearly to the
  *      integration point from the first two fluid nodes along the sampling
  *      direction (the paper copies it from the first, R6).
+ *  R21 the "free flow" outlet of the sedimentation case (Sec. 3.2) is a
+ *      zero normal gradient: the populations entering the last column from
+ *      beyond the edge copy those of the column before it, after streaming.
  *  R19 the volume-integral force of Eq. Angotforce is the penalization
  *      force reversed, sum over solid nodes of rho (chi/eta)(u - u_s) (the
  *      printed formula has lost the 1/eta and writes the limit as eta to
@@ -78,7 +81,7 @@ static const double WGT[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
 static const double CS2 = 1.0 / 3.0;
 
 /* boundary kinds, per side x_lo, x_hi, y_lo, y_hi */
-enum { BC_PERIODIC = 0, BC_INLET = 1, BC_OUTLET = 2, BC_SYMMETRY = 3, BC_NOSLIP = 4 };
+enum { BC_PERIODIC = 0, BC_INLET = 1, BC_OUTLET = 2, BC_SYMMETRY = 3, BC_NOSLIP = 4, BC_OUTLET_FREE = 5 };
 enum { COLL_BGK = 0, COLL_TRT = 1 };
 enum { FORCING_PAPER = 0, FORCING_SPLIT = 1 };
 enum { BODY_NONE = 0, BODY_DISK = 1, BODY_NACA = 2 };
@@ -352,6 +355,7 @@ void orc_fields(const orc_config *cfg, const orc_body *b, const uint8_t *chi, co
  *   symmetry: specular reflection at the wall half a cell beyond the edge
  *   outlet  : convective condition (Yang), f_a^{n+1}(N-1) =
  *             (f_a^n(N-1) + U_c f_a^{n+1}(N-2)) / (1 + U_c), U_c = |u_in|
+ *   free outlet: zero normal gradient, f_a^{n+1}(N-1) = f_a^{n+1}(N-2)
  * f_prev is the pre-collision field of the current step (for the outlet). */
 static int mirror_y(int a) {
   /* flip c_y */
@@ -378,7 +382,7 @@ void orc_stream(const orc_config *cfg, const double *ft, const double *f_prev, d
         } else if (si < 0 || si >= nx) {
           int side = si < 0 ? 0 : 1;
           int kind = cfg->bc[side];
-          if (kind == BC_OUTLET) continue; /* pass 2 */
+          if (kind == BC_OUTLET || kind == BC_OUTLET_FREE) continue; /* pass 2 */
           if (kind == BC_INLET) {
             double cu = CX[a] * cfg->u_in[0] + CY[a] * cfg->u_in[1];
             v = ft[idx(cfg, OPP[a], i, j)] + 2.0 * WGT[a] * 1.0 * cu / CS2;
@@ -407,6 +411,13 @@ void orc_stream(const orc_config *cfg, const double *ft, const double *f_prev, d
         f_out[idx(cfg, a, i, j)] =
             (f_prev[idx(cfg, a, i, j)] + uc * f_out[idx(cfg, a, i - 1, j)]) / (1.0 + uc);
       }
+  }
+  /* pass 2: free outlet on the x_hi side */
+  if (cfg->bc[1] == BC_OUTLET_FREE) {
+    int i = nx - 1;
+    for (int j = 0; j < ny; ++j)
+      for (int a = 0; a < Q; ++a)
+        if (CX[a] < 0) f_out[idx(cfg, a, i, j)] = f_out[idx(cfg, a, i - 1, j)];
   }
 }
 

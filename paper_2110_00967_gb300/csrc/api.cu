@@ -103,17 +103,19 @@ const char *check_config(const vplbm_config *c) {
   if (c->collision == VPLBM_TRT && !(c->lambda_trt > 0.0)) return "lambda_trt must be > 0";
   if (!(c->eta > 0.0)) return "eta must be > 0";
   if (c->sim_every < 0 || c->max_sim_points < 0 || c->history_len < 0) return "negative count";
+  if (c->sim_order != 0 && c->sim_order != 1) return "sim_order must be 0 or 1";
   for (int k = 0; k < 2; ++k)
     if (!std::isfinite(c->u_in[k]) || !std::isfinite(c->body_force[k]) || !std::isfinite(c->u_ref[k]))
       return "non-finite velocity or force";
   if (c->u_ref[0] * c->u_ref[0] + c->u_ref[1] * c->u_ref[1] > 0.09) return "|u_ref| must be below 0.3";
   const int x0 = c->bc[0], x1 = c->bc[1], y0 = c->bc[2], y1 = c->bc[3];
   auto xok = [](int b) {
-    return b == VPLBM_PERIODIC || b == VPLBM_INLET_BB || b == VPLBM_OUTLET_CONVECTIVE || b == VPLBM_NOSLIP_BB;
+    return b == VPLBM_PERIODIC || b == VPLBM_INLET_BB || b == VPLBM_OUTLET_CONVECTIVE ||
+           b == VPLBM_OUTLET_FREE || b == VPLBM_NOSLIP_BB;
   };
   auto yok = [](int b) { return b == VPLBM_PERIODIC || b == VPLBM_SYMMETRY || b == VPLBM_NOSLIP_BB; };
   if (!xok(x0) || !xok(x1) || !yok(y0) || !yok(y1)) return "side condition not allowed on that side";
-  if (x0 == VPLBM_OUTLET_CONVECTIVE) return "the convective outlet is an x_hi condition";
+  if (x0 == VPLBM_OUTLET_CONVECTIVE || x0 == VPLBM_OUTLET_FREE) return "outlets are x_hi conditions";
   if ((x0 == VPLBM_PERIODIC) != (x1 == VPLBM_PERIODIC)) return "x periodicity must hold on both sides";
   if ((y0 == VPLBM_PERIODIC) != (y1 == VPLBM_PERIODIC)) return "y periodicity must hold on both sides";
   return nullptr;
@@ -283,6 +285,7 @@ StepArgs step_args(vplbm_ctx *c, int src, bool do_sim) {
   for (int k = 0; k < 3; ++k) a.sim_const[k] = c->sim_const[k];
   a.sim_nodes = c->sim_nodes;
   a.n_sim = c->n_sim;
+  a.sim_order = c->cfg.sim_order;
   a.sim_blocks = do_sim ? (c->n_sim + kThreads - 1) / kThreads : 0;
   a.hist = c->hist;
   a.hist_len = effective_hist(c->cfg);

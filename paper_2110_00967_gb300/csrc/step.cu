@@ -183,6 +183,21 @@ __device__ __noinline__ FixAcc<typename Store<S>::T> sim_point(const StepArgs &p
       if (first < 0) first = qj * p.L.nx + qi;
       T s3[3];
       node_stress<S, kGather>(buf, prev, p.L, Consts<T>(p), qi, qj, s3);
+      if (p.sim_order == 1) {
+        // first order: extrapolated to the point along the direction from
+        // the next node, where that node is fluid and inside the lattice
+        const int ni = qi + cx_of(sp.dir), nj = qj + cy_of(sp.dir);
+        if (ni >= 0 && ni < p.L.nx && nj >= 0 && nj < p.L.ny &&
+            !(p.chi[(int64_t)nj * p.L.pitch + ni] & kSolid)) {
+          T s3n[3];
+          node_stress<S, kGather>(buf, prev, p.L, Consts<T>(p), ni, nj, s3n);
+          const int c2 = cx_of(sp.dir) * cx_of(sp.dir) + cy_of(sp.dir) * cy_of(sp.dir);
+          const T t = (T)(((x - qi) * cx_of(sp.dir) + (y - qj) * cy_of(sp.dir)) / (double)c2);
+          s3[0] += t * (s3n[0] - s3[0]);
+          s3[1] += t * (s3n[1] - s3[1]);
+          s3[2] += t * (s3n[2] - s3[2]);
+        }
+      }
       sig[0] += s3[0];
       sig[1] += s3[1];
       sig[2] += s3[2];

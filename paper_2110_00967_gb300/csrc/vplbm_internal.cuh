@@ -319,6 +319,8 @@ __device__ __forceinline__ typename Store<S>::T gather(const S *post,
     const T uc = LatC<T>::uc(L);
     return (old + uc * inner) / ((T)1 + uc);
   }
+  if (cx_of(a) < 0 && i == L.nx - 1 && L.bc[1] == VPLBM_OUTLET_FREE)
+    return gather_core(post, L, a, i - 1, j);  // free outlet: zero normal gradient
   return gather_core(post, L, a, i, j);
 }
 
@@ -419,6 +421,7 @@ struct StepArgs {
   const SimPoint *sim_pts;
   int32_t *sim_nodes;    // [n_sim]
   int32_t n_sim;
+  int32_t sim_order;     // 0: stress copied from the sampled node; 1: extrapolated linearly
   int32_t sim_blocks;    // leading blocks that evaluate SIM (0: SIM not due)
   double *hist;          // [hist_len][6]
   int32_t hist_len;

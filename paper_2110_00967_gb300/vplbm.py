@@ -19,7 +19,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
 F64, F32, F16_OFS, BF16_OFS = range(4)
 BGK, TRT = 0, 1
 FORCING_PAPER, FORCING_SPLIT = 0, 1
-PERIODIC, INLET_BB, OUTLET_CONVECTIVE, SYMMETRY, NOSLIP_BB = range(5)
+PERIODIC, INLET_BB, OUTLET_CONVECTIVE, SYMMETRY, NOSLIP_BB, OUTLET_FREE = range(6)
 BODY_NONE, BODY_DISK, BODY_NACA4 = range(3)
 MEM, SIM, ANGOT = 0, 1, 2
 
@@ -37,7 +37,7 @@ class vplbm_config(C.Structure):
     _fields_ = [
         ("nx", C.c_int32), ("ny", C.c_int32), ("dtype", C.c_int32), ("collision", C.c_int32),
         ("forcing", C.c_int32), ("bc", C.c_int32 * 4), ("sim_every", C.c_int32),
-        ("max_sim_points", C.c_int32), ("history_len", C.c_int32),
+        ("max_sim_points", C.c_int32), ("history_len", C.c_int32), ("sim_order", C.c_int32),
         ("tau_plus", C.c_double), ("lambda_trt", C.c_double), ("eta", C.c_double),
         ("u_in", C.c_double * 2), ("body_force", C.c_double * 2), ("u_ref", C.c_double * 2),
     ]
@@ -56,12 +56,13 @@ class vplbm_body(C.Structure):
 def config(nx, ny, dtype=F32, collision=TRT, forcing=FORCING_PAPER,
            bc=(PERIODIC, PERIODIC, PERIODIC, PERIODIC), sim_every=1, max_sim_points=0,
            history_len=0, tau_plus=0.8, lambda_trt=1.0 / 6.0, eta=1e-6, u_in=(0.0, 0.0),
-           body_force=(0.0, 0.0), u_ref=(0.0, 0.0)) -> vplbm_config:
+           body_force=(0.0, 0.0), u_ref=(0.0, 0.0), sim_order=0) -> vplbm_config:
     c = vplbm_config()
     c.nx, c.ny, c.dtype, c.collision, c.forcing = nx, ny, dtype, collision, forcing
     for k in range(4):
         c.bc[k] = bc[k]
     c.sim_every, c.max_sim_points, c.history_len = sim_every, max_sim_points, history_len
+    c.sim_order = sim_order
     c.tau_plus, c.lambda_trt, c.eta = tau_plus, lambda_trt, eta
     c.u_in[0], c.u_in[1] = u_in
     c.body_force[0], c.body_force[1] = body_force
@@ -417,7 +418,7 @@ class Lattice:
 # ---------------------------------------------------------------------------
 _DTYPES = {"f64": F64, "f32": F32, "f16": F16_OFS, "bf16": BF16_OFS}
 _BCS = {"periodic": PERIODIC, "inlet": INLET_BB, "outlet": OUTLET_CONVECTIVE,
-        "symmetry": SYMMETRY, "noslip": NOSLIP_BB}
+        "symmetry": SYMMETRY, "noslip": NOSLIP_BB, "outlet_free": OUTLET_FREE}
 _KINDS = {"none": BODY_NONE, "disk": BODY_DISK, "naca": BODY_NACA4}
 
 

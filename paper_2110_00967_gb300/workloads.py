@@ -20,6 +20,7 @@ import numpy as np
 
 # side kinds and options by name (mapped to the ABI values by the callers)
 PERIODIC, INLET, OUTLET, SYMMETRY, NOSLIP = "periodic", "inlet", "outlet", "symmetry", "noslip"
+OUTLET_FREE = "outlet_free"
 
 
 @dataclass(frozen=True)
@@ -133,6 +134,45 @@ def sedimentation(estimator: str = "mem", steps: int = 100_000) -> Workload:
         body=Body("disk", length=d_lu, x_c=-0.5 + 0.75 * d_lu, y_c=1599.5 - 4.0 * d_lu,
                   moving=True, density_ratio=1.03, gravity=(0.0, -g_lu), estimator=estimator),
         steps=steps)
+
+
+# density ratios of the paper's sedimentation runs (Sec. 3.2); the third value
+# is printed as a repeat of the first, read as 1.01 (between the terminal
+# Reynolds numbers 1.03 and 8.33 it is listed with)
+RHO_R_PAPER = (1.0015, 1.003, 1.01, 1.03)
+RE_TERMINAL_PAPER = (0.52, 1.03, 3.23, 8.33)
+
+
+def sedimentation_paper(density_ratio: float = 1.03, estimator: str = "sim",
+                        steps: int = 1000, length_d: int = 120, width_d: int = 8) -> Workload:
+    """The paper's own sedimentation case (Sec. 3.2): disk D = 26, TRT tau = 0.6,
+    a channel width_d D wide and length_d D long with no-slip side walls, a
+    zero-velocity inlet at the top and a free outlet at the bottom, the disk
+    released at rest 0.75 D from the left wall and 4 D below the top.  The fall
+    runs along +x (the top is x_lo, the bottom x_hi, the left wall y_lo: the
+    paper's frame turned by a quarter turn, which keeps the sense of rotation),
+    so that the inlet and outlet sit on the x sides where the library has them.
+    Gravity in lattice units: D = 0.1 cm on 26 nodes gives dx = 0.1/26 cm;
+    nu = 1/30 in lattice units and 0.1 cm^2/s gives dt = dx^2 / 3 s, so
+    |g| = 980 cm/s^2 becomes 980 dt^2 / dx."""
+    d_lu, tau = 26.0, 0.6
+    dx, dt = 0.1 / d_lu, sedimentation_paper_dt()
+    g_lu = 980.0 * dt * dt / dx
+    nx, ny = int(length_d * d_lu), int(width_d * d_lu)
+    return Workload(
+        name=f"sedimentation-paper-{nx}x{ny}-rho{density_ratio}-{estimator}", nx=nx, ny=ny,
+        dtype="f32", collision="trt", tau_plus=tau, u_in=(0.0, 0.0),
+        bc=(INLET, OUTLET_FREE, NOSLIP, NOSLIP),
+        body=Body("disk", length=d_lu, x_c=-0.5 + 4.0 * d_lu, y_c=-0.5 + 0.75 * d_lu,
+                  moving=True, density_ratio=density_ratio, gravity=(g_lu, 0.0),
+                  estimator=estimator),
+        steps=steps)
+
+
+def sedimentation_paper_dt() -> float:
+    """Physical seconds per lattice step of the paper's sedimentation case."""
+    dx = 0.1 / 26.0
+    return (1.0 / 30.0) * dx * dx / 0.1
 
 
 SERVING_GRIDS = ((512, 256), (768, 384), (1024, 512), (1536, 768), (2048, 1024))

@@ -2,7 +2,7 @@
 import oracle as o
 
 _BCS = {"periodic": o.BC_PERIODIC, "inlet": o.BC_INLET, "outlet": o.BC_OUTLET,
-        "symmetry": o.BC_SYMMETRY, "noslip": o.BC_NOSLIP}
+        "symmetry": o.BC_SYMMETRY, "noslip": o.BC_NOSLIP, "outlet_free": o.BC_OUTLET_FREE}
 _KINDS = {"none": o.BODY_NONE, "disk": o.BODY_DISK, "naca": o.BODY_NACA}
 
 

@@ -71,6 +71,7 @@ MOVE_BCS = [
     ("periodic", "periodic", "noslip", "noslip"),
     ("noslip", "noslip", "symmetry", "symmetry"),
     ("noslip", "noslip", "noslip", "noslip"),
+    ("noslip", "outlet_free", "noslip", "noslip"),
 ]
 
 
@@ -256,13 +257,51 @@ def test_moving_disk_fp64_trajectory():
         assert rel_linf(lat.get_f(), f) <= 1e-10
 
 
-@pytest.mark.parametrize("est", ["mem", "sim"])
-def test_sedimentation_full_size_first_1000_steps(est):
-    """The 400 x 1600 sedimentation box (FP32 lattice, FP64 rigid body driven by
-    MEM or by SIM, chi re-rasterised every step) against the FP64 oracle over the
-    first 1000 steps: per-step forces within 1e-3 of the largest oracle force,
-    the body's velocity within 1e-3 relative and its position within 1e-4."""
-    w = W.sedimentation(est, steps=1000)
+def test_moving_disk_fp64_channel_with_free_outlet():
+    """A disk falling along +x in a channel with a zero-velocity inlet above it
+    and the free outlet below (the side conditions of the paper's
+    sedimentation case, reading R21), FP64: trajectory, fields and mask match
+    the oracle after 300 steps, for MEM and SIM."""
+    for est in ("mem", "sim"):
+        w = W.Workload(name="fall-channel", nx=120, ny=40, dtype="f64", collision="trt",
+                       tau_plus=0.6, u_in=(0.0, 0.0), bc=("inlet", "outlet_free", "noslip", "noslip"),
+                       body=W.Body("disk", length=10.0, x_c=25.2, y_c=14.6, moving=True,
+                                   density_ratio=1.5, gravity=(6e-4, 0.0), estimator=est),
+                       steps=300)
+        lat = lattice(w)
+        lat.step(w.steps)
+        cfg, ob, chi, f, pts = oracle_setup(w)
+        _, _, bh, bad = o.run(cfg, ob, f, chi, w.steps, estimator=1 if est == "sim" else 0,
+                              sim_pts=pts)
+        assert bad == 0
+        got, ref = lat.get_body(), bh[-1]
+        assert abs(got[0] - ref[0]) < 1e-10 * abs(ref[0])
+        assert abs(got[3] - ref[3]) <= 1e-9 * abs(ref[3])
+        assert abs(got[5] - ref[5]) <= 1e-9 * abs(ref).max()
+        assert got[0] > 25.2 + 1.0  # it fell more than a cell
+        assert np.array_equal(lat.get_mask(), chi)
+        assert rel_linf(lat.get_f(), f) <= 1e-10
+
+
+SEDIMENTATION_CASES = {
+    "box-mem": lambda: W.sedimentation("mem", steps=1000),
+    "box-sim": lambda: W.sedimentation("sim", steps=1000),
+    # the paper's channel (D = 26, free outlet), heaviest and lightest disks
+    "paper-1.03-mem": lambda: W.sedimentation_paper(1.03, "mem", steps=1000),
+    "paper-1.03-sim": lambda: W.sedimentation_paper(1.03, "sim", steps=1000),
+    "paper-1.0015-sim": lambda: W.sedimentation_paper(1.0015, "sim", steps=1000),
+}
+
+
+@pytest.mark.parametrize("case", list(SEDIMENTATION_CASES))
+def test_sedimentation_full_size_first_1000_steps(case):
+    """The sedimentation cases at full size (FP32 lattice, FP64 rigid body driven
+    by MEM or by SIM, chi re-rasterised every step) against the FP64 oracle over
+    the first 1000 steps: per-step forces within 1e-3 of the largest oracle
+    force, the body's fall velocity within 1e-3 relative and its position
+    within 1e-4."""
+    w = SEDIMENTATION_CASES[case]()
+    est = w.body.estimator
     lat = lattice(w, history_len=1000)
     lat.step(w.steps)
     cfg, ob, chi, f, pts = oracle_setup(w)
@@ -274,9 +313,11 @@ def test_sedimentation_full_size_first_1000_steps(est):
     scale = np.abs(ref[:, :2]).max()
     assert np.abs(got[:, :2] - ref[:, :2]).max() <= 1e-3 * scale
     b = lat.get_body()
-    assert abs(b[4] - bh[-1][4]) <= 1e-3 * abs(bh[-1][4])  # u_y
-    assert abs(b[1] - bh[-1][1]) <= 1e-4  # y
-    assert b[4] < 0 and b[1] < w.body.y_c  # it falls
+    k = 0 if w.body.gravity[0] != 0 else 1  # the fall axis
+    assert abs(b[3 + k] - bh[-1][3 + k]) <= 1e-3 * abs(bh[-1][3 + k])
+    assert abs(b[k] - bh[-1][k]) <= 1e-4
+    g = w.body.gravity[k]
+    assert b[3 + k] * g > 0 and (b[k] - (w.body.x_c, w.body.y_c)[k]) * g > 0  # it falls
 
 
 # ---------------------------------------------------------------------------
@@ -428,6 +469,34 @@ def test_volume_integral_force_per_step(case):
     assert scale > 0
     assert np.abs(got[:, :2] - ref[:, :2]).max() <= tol * scale
     np.testing.assert_array_equal(lat.force_angot()[:2], got[-1, :2])
+
+
+@pytest.mark.parametrize("case", ["disk-f64", "naca-f32"])
+def test_first_order_sim_per_step(case):
+    """SIM with the stress extrapolated linearly to each point (reading R20)
+    against the oracle's, step by step on the same pre-collision states: 1e-12
+    relative in FP64, 1e-3 of the largest value in FP32; and the copied stress
+    of order 0 lies much further from it than the GPU does."""
+    if case == "disk-f64":
+        w, n, tol = W.disk_channel(), 300, 1e-12
+    else:
+        w, n, tol = W.naca(12.0, dtype="f32", nx=512, ny=256), 200, 1e-3
+    lat = lattice(w, history_len=n, sim_order=1)
+    lat.step(n)
+    got = lat.history(V.SIM, n)
+    cfg, body, chi, f, pts = oracle_setup(w)
+    ref, ref0 = np.zeros((n, 3)), np.zeros((n, 3))
+    for k in range(n):
+        ref[k], _, missing, _ = o.sim_order(cfg, body, chi, f, pts, 1)
+        assert missing == 0
+        ref0[k] = o.sim(cfg, body, chi, f, pts)[0]
+        o.run(cfg, body, f, chi, 1, histories=False)
+    scale = np.abs(ref[:, :2]).max()
+    assert scale > 0
+    err = np.abs(got[:, :2] - ref[:, :2]).max()
+    assert err <= tol * scale
+    # the two orders differ by far more than the GPU's distance from order 1
+    assert np.abs(ref0[:, :2] - ref[:, :2]).max() > 10 * err
 
 
 def test_history_ring_wraps():

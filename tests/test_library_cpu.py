@@ -46,7 +46,7 @@ def test_workspace_bytes_and_config_checks():
         dict(bc=(V.PERIODIC, V.INLET_BB, V.PERIODIC, V.PERIODIC)),
         dict(bc=(V.INLET_BB, V.OUTLET_CONVECTIVE, V.INLET_BB, V.SYMMETRY)),
         dict(bc=(V.INLET_BB, V.OUTLET_CONVECTIVE, V.PERIODIC, V.SYMMETRY)),
-        dict(collision=V.TRT, lambda_trt=0.0),
+        dict(collision=V.TRT, lambda_trt=0.0), dict(sim_order=2), dict(sim_order=-1),
     ]
     for over in bad:
         c = V.config(**{**dict(nx=64, ny=32), **over})

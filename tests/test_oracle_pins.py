@@ -292,6 +292,30 @@ def test_convective_outlet_special_cases():
         np.testing.assert_allclose(out[a, :, -1], ref[a, :, -1], rtol=0, atol=4e-16)
 
 
+def test_free_outlet_is_the_convective_limit():
+    """The free outlet (reading R21) is the convective outlet as U_c grows
+    without bound: equal to 1e-10 at U_c = 1e12 on random fields (with no-slip
+    and periodic y sides, so that corners are covered); every population that
+    does not enter through the outlet is streamed the same way; a field
+    uniform in x is a fixed point."""
+    rng = np.random.default_rng(21)
+    nx, ny = 9, 5
+    ft, prev = rng.random((9, ny, nx)), rng.random((9, ny, nx))
+    for ys in (o.BC_NOSLIP, o.BC_PERIODIC):
+        free = o.stream(o.make_config(nx, ny, bc=(o.BC_NOSLIP, o.BC_OUTLET_FREE, ys, ys)), ft, prev)
+        conv = o.stream(o.make_config(nx, ny, bc=(o.BC_NOSLIP, o.BC_OUTLET, ys, ys),
+                                      u_in=(1e12, 0.0)), ft, prev)
+        assert np.abs(free - conv).max() <= 1e-10
+        keep = np.ones_like(free, bool)
+        keep[[3, 6, 7], :, -1] = False
+        wall = o.stream(o.make_config(nx, ny, bc=(o.BC_NOSLIP, o.BC_NOSLIP, ys, ys)), ft, prev)
+        assert np.array_equal(free[keep], wall[keep])
+    uni = np.repeat(rng.random((9, ny, 1)), nx, axis=2)
+    ref = o.stream(o.make_config(nx, ny, bc=(o.BC_PERIODIC, o.BC_PERIODIC, 0, 0)), uni, uni)
+    out = o.stream(o.make_config(nx, ny, bc=(o.BC_NOSLIP, o.BC_OUTLET_FREE, 0, 0)), uni, uni)
+    assert np.array_equal(out[[3, 6, 7], :, -1], ref[[3, 6, 7], :, -1])
+
+
 # --------------------------------------------------------------------------
 # whole steps: conservation and closed-form flows
 # --------------------------------------------------------------------------
