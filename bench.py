@@ -389,8 +389,8 @@ def run_sedimentation(args, rank, world, local_rank, paper=False):
         "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed_ms / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": ("sedimentation-paper-3120x208-f32-disk26-rho1.0015,1.003,1.01,"
-                                "1.03-mem,sim-inlet0-free-outlet" if paper else
+        "config": {"workload": (f"sedimentation-paper-{works[0].nx}x{works[0].ny}-f32-disk26-"
+                                "rho1.0015,1.003,1.01,1.03-mem,sim-inlet0-free-outlet" if paper else
                                 "sedimentation-400x1600-f32-disk50-rho1.03-mem,sim"),
                    "grid": [works[0].nx, works[0].ny], "instances": len(lats), "tau_plus": 0.6,
                    "gravity": max(abs(g) for g in works[0].body.gravity),
@@ -632,7 +632,7 @@ def main(argv=None):
                          "mix of NACA solves run to convergence; disk: the FP64 disk channel; "
                          "naca-paper: the paper's C = 278 NACA grid at its angles; "
                          "sedimentation-paper: the paper's D = 26 channel, four density "
-                         "ratios, MEM and SIM (about 203,000 steps reach 1 s)")
+                         "ratios, MEM and SIM (20,280 steps per physical second)")
     ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
     ap.add_argument("--cap", type=int, default=20000, help="serving: step cap per request")
     ap.add_argument("--memory-gb", type=int, default=40, help="serving: device-memory budget")
