@@ -527,10 +527,19 @@ def run_disk(args, rank, world, local_rank):
     return line
 
 
-def run_naca_paper(args, rank, world, local_rank):
+SIM_VARIANTS = ((107, 0), (213, 0), (425, 0), (849, 0), (1697, 0), (3393, 0), (849, 1), (3393, 1))
+
+
+def run_naca_paper(args, rank, world, local_rank, sim_variants=False):
     """The paper's own NACA 0012 case (C = 278, U0 = 0.0599, tau 0.55, 3614 x
     1946 FP32) at the angles 0, 4, ..., 28 degrees as one batch; reports the
-    MLUPS of the timed steps and the Cd/Cl means over them (MEM and SIM)."""
+    MLUPS of the timed steps and the Cd/Cl means over them (MEM and SIM).
+    With `sim_variants`, the same case at 12 degrees once per SIM variant
+    (point counts 107 .. 3393, stress copied or extrapolated to first order):
+    the body is fixed, so every lattice carries the same flow and only the
+    SIM estimate differs."""
+    import dataclasses
+
     import torch
     from paper_2110_00967_gb300 import vplbm as V
     from paper_2110_00967_gb300 import workloads as W
@@ -538,8 +547,15 @@ def run_naca_paper(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    works = [W.naca_paper(a, dtype=args.dtype) for a in W.PAPER_ANGLES]
-    lats = [V.Lattice(V.config_of(w), device=dev) for w in works]
+    if sim_variants:
+        base = W.naca_paper(12.0, dtype=args.dtype)
+        works = [base.with_(body=dataclasses.replace(base.body, n_sim_points=n))
+                 for n, _ in SIM_VARIANTS]
+        lats = [V.Lattice(V.config_of(w, sim_order=order, max_sim_points=4096), device=dev)
+                for w, (_, order) in zip(works, SIM_VARIANTS)]
+    else:
+        works = [W.naca_paper(a, dtype=args.dtype) for a in W.PAPER_ANGLES]
+        lats = [V.Lattice(V.config_of(w), device=dev) for w in works]
     for w, lat in zip(works, lats):
         lat.set_body(V.body_of(w))
     batch = V.Batch(lats, stream=stream)
@@ -559,12 +575,19 @@ def run_naca_paper(args, rank, world, local_rank):
     elapsed_ms = reduce_max(start.elapsed_time(end), world, dev)
     q = 0.5 * 0.0599 ** 2 * 278.0
     coeffs = {}
-    for w, lat in zip(works, lats):
+    for k, (w, lat) in enumerate(zip(works, lats)):
         lat.check()
         sums, n = lat.sums()
-        coeffs[f"{w.body.angle_deg:g}"] = {
+        key = (f"n{SIM_VARIANTS[k][0]}-order{SIM_VARIANTS[k][1]}" if sim_variants
+               else f"{w.body.angle_deg:g}")
+        coeffs[key] = {
             "cd_mem": sums[0] / n[0] / q, "cl_mem": sums[1] / n[0] / q,
             "cd_sim": sums[3] / n[1] / q, "cl_sim": sums[4] / n[1] / q}
+    if sim_variants:
+        ref = coeffs["n3393-order0"]
+        for c in coeffs.values():
+            c["rel_to_n3393_order0"] = [(c["cd_sim"] - ref["cd_sim"]) / abs(ref["cd_sim"]),
+                                        (c["cl_sim"] - ref["cl_sim"]) / abs(ref["cl_sim"])]
     nodes = works[0].nx * works[0].ny * len(lats)
     bpl = BYTES_PER_LUP[args.dtype]
     lattice_step_ms = elapsed_ms / (args.steps * len(lats))
@@ -579,7 +602,9 @@ def run_naca_paper(args, rank, world, local_rank):
         "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed_ms / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"naca0012-paper-3614x1946-{args.dtype}-alpha0..28",
+        "config": {"workload": (f"naca0012-paper-3614x1946-{args.dtype}-alpha12-sim-variants"
+                                if sim_variants else
+                                f"naca0012-paper-3614x1946-{args.dtype}-alpha0..28"),
                    "grid": [works[0].nx, works[0].ny], "instances": len(lats), "chord": 278,
                    "u0": 0.0599, "tau_plus": 0.55, "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -625,14 +650,16 @@ def main(argv=None):
                          "of the whole region)")
     ap.add_argument("--workload",
                     choices=("naca", "sedimentation", "serving", "disk", "naca-paper",
-                             "sedimentation-paper"),
+                             "sedimentation-paper", "sim-variants"),
                     default="naca",
                     help="naca: the five NACA 0012 lattices (the benchmark); sedimentation: "
                          "the 400 x 1600 falling-disk box, MEM and SIM runs; serving: a seeded "
                          "mix of NACA solves run to convergence; disk: the FP64 disk channel; "
                          "naca-paper: the paper's C = 278 NACA grid at its angles; "
                          "sedimentation-paper: the paper's D = 26 channel, four density "
-                         "ratios, MEM and SIM (20,280 steps per physical second)")
+                         "ratios, MEM and SIM (20,280 steps per physical second); sim-variants: "
+                         "the paper's NACA case at 12 degrees once per SIM point count and "
+                         "order")
     ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
     ap.add_argument("--cap", type=int, default=20000, help="serving: step cap per request")
     ap.add_argument("--memory-gb", type=int, default=40, help="serving: device-memory budget")
@@ -663,8 +690,9 @@ def main(argv=None):
             line = run_serving(args, rank, world, local_rank)
         elif args.workload == "disk":
             line = run_disk(args, rank, world, local_rank)
-        elif args.workload == "naca-paper":
-            line = run_naca_paper(args, rank, world, local_rank)
+        elif args.workload in ("naca-paper", "sim-variants"):
+            line = run_naca_paper(args, rank, world, local_rank,
+                                  sim_variants=args.workload == "sim-variants")
         else:
             line = run_ours(args, rank, world, local_rank)
     if line is not None:
