@@ -57,8 +57,9 @@ def config_block(dtype: str = "f32", extra=None):
          "chord": 200, "reynolds": 1000, "tau_plus": 0.53, "collision": "trt-lambda-1/6",
          "storage": "f32" if dtype == "f32" else f"{dtype} offsets from feq(1, u_in)",
          "forces_per_step": ["mem", "sim-849"],
-         "l2": f"inputs larger than L2: 5 lattices x {mb} MB ping-pong, stepped side by side "
-               "(ncu range replay: DRAM traffic 153.5 MB per lattice step, 151.0 algorithmic)"}
+         "l2": f"inputs larger than L2: 5 lattices x {mb} MB ping-pong, stepped side by side"
+               + (" (ncu range replay: DRAM traffic 154.0 MB per lattice step, 151.0 algorithmic)"
+                  if dtype == "f32" else "")}
     if extra:
         c.update(extra)
     return c

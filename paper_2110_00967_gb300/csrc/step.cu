@@ -843,14 +843,17 @@ __device__ __forceinline__ void collide2(const V (&h)[9], V drho, V dux, V duy, 
 }
 
 // ---------------------------------------------------------------------------
-// bulk kernel for 16-bit storage: two nodes per thread.  With 2-byte values a
-// load instruction per population and node moves too few bytes to keep HBM
-// busy, so each thread takes the nodes (i, i+1), i even, of a tile row: one
-// aligned 32-bit load per plane brings both values of planes with c_x = 0;
-// for c_x = +1 (sources i-1, i) and c_x = -1 (sources i+1, i+2) the odd
-// neighbour comes from the next lane by a warp shuffle (one extra 2-byte load
-// at the warp's edge), and both results leave in one 32-bit store per plane.
-// The collision of the two nodes runs in packed f32x2 (collide2).
+// bulk kernel for 16-bit storage: four nodes per thread.  HBM stays busy
+// only with enough bytes in flight per SM; with 2-byte values and one node per
+// thread that needs more threads than the registers allow.  So each thread
+// takes the nodes i .. i+3 (i a multiple of 4) of a tile row, one warp per
+// row: one aligned 64-bit load per plane brings four values, kept packed (two
+// 32-bit words per plane, 18 registers for 4 nodes).  For c_x = +1 (sources
+// i-1 .. i+2) and c_x = -1 (sources i+1 .. i+4) the value beyond the thread's
+// four comes from the next lane by a warp shuffle (one extra 2-byte load at
+// the warp's edge) and a funnel shift realigns the words.  The nodes are
+// collided two at a time in packed f32x2 (collide2) and leave in one 64-bit
+// store per plane.
 // ---------------------------------------------------------------------------
 template <typename S>
 struct Pair16;
@@ -877,55 +880,22 @@ struct Pair16<__nv_bfloat16> {
   }
 };
 
+// (lo half of b, hi half of a) -> the pair starting one value later
+__device__ __forceinline__ uint32_t shift16(uint32_t a, uint32_t b) {
+  return __funnelshift_r(a, b, 16);
+}
+
+// the collision of the node pair whose pre-collision values are the packed
+// words w[a]; returns the packed post-collision words and rho
 template <typename S, bool kForce>
-__global__ void __launch_bounds__(kThreads / 2) bulk16_kernel(const StepArgs p) {
+__device__ __forceinline__ F2 collide_pair16(const StepArgs &p, const uint32_t (&w)[9],
+                                             uint32_t (&out)[9]) {
   using P = Pair16<S>;
-  const int ti = blockIdx.x, tj = blockIdx.y;
   const Lattice &L = p.L;
-  const int lane = threadIdx.x & 31;
-  const int i = ti * kTileX + 2 * threadIdx.x;  // the thread's nodes i, i + 1
-  const int j = tj * kTileY + threadIdx.y;
-  // every lane loads from inside its row (clamped), so that the shuffles see
-  // all 32 lanes; results of clamped lanes are never stored
-  const int ic = i < L.pitch - 2 ? i : L.pitch - 2;
-  const S *__restrict__ src = static_cast<const S *>(p.src);
-  float lo_v[9], hi_v[9];
-#pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    int r = j - cy_of(a);
-    r = r < 0 ? 0 : (r > L.ny - 1 ? L.ny - 1 : r);
-    const S *row = src + (int64_t)a * L.plane + (int64_t)r * L.pitch;
-    const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(row + ic));
-    if (cx_of(a) == 0) {
-      lo_v[a] = P::lo(w);
-      hi_v[a] = P::hi(w);
-    } else if (cx_of(a) > 0) {  // sources i - 1 (the left lane's high half) and i
-      uint32_t left = __shfl_up_sync(0xffffffffu, w, 1);
-      if (lane == 0)
-        left = ic >= 1 ? ((uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic - 1)) << 16)
-                       : 0u;
-      lo_v[a] = P::hi(left);
-      hi_v[a] = P::lo(w);
-    } else {  // sources i + 1 and i + 2 (the right lane's low half)
-      uint32_t right = __shfl_down_sync(0xffffffffu, w, 1);
-      if (lane == 31)
-        right = ic + 2 < L.pitch ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic + 2))
-                                 : 0u;
-      lo_v[a] = P::hi(w);
-      hi_v[a] = P::lo(right);
-    }
-  }
-  {
-    const ForceRegion reg = *p.reg_src;
-    if (ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1) return;  // special kernel
-  }
-  if (j < 1 || j > L.ny - 2) return;  // edge rows: special kernel
-  const bool lo_ok = i >= 1 && i <= L.nx - 2, hi_ok = i + 1 <= L.nx - 2;
-  if (!lo_ok && !hi_ok) return;
   const Consts<float> cst(p);
   F2 h[9];
 #pragma unroll
-  for (int a = 0; a < 9; ++a) h[a] = vpair(lo_v[a], hi_v[a]);
+  for (int a = 0; a < 9; ++a) h[a] = vpair(P::lo(w[a]), P::hi(w[a]));
   const F2 drho = vadd(vadd(vadd(h[0], h[1]), vadd(h[2], h[3])),
                        vadd(vadd(vadd(h[4], h[5]), vadd(h[6], h[7])), h[8]));
   F2 djx = vadd(vadd(vsub(h[1], h[3]), vsub(h[5], h[6])), vsub(h[8], h[7]));
@@ -943,21 +913,83 @@ __global__ void __launch_bounds__(kThreads / 2) bulk16_kernel(const StepArgs p) 
     collide2<F2, float, false>(h, drho, vmul(vfma(drho, vsplat(-cst.urx), djx), inv),
                                vmul(vfma(drho, vsplat(-cst.ury), djy), inv), F2{}, F2{}, cst, o);
   }
-  S *dst = static_cast<S *>(p.dst) + (int64_t)j * L.pitch + i;
-  if (lo_ok && hi_ok) {
 #pragma unroll
-    for (int a = 0; a < 9; ++a)
-      *reinterpret_cast<uint32_t *>(dst + (int64_t)a * L.plane) = P::pack(vlo(o[a]), vhi(o[a]));
-  } else {
+  for (int a = 0; a < 9; ++a) out[a] = P::pack(vlo(o[a]), vhi(o[a]));
+  return rho;
+}
+
+__device__ __forceinline__ bool rho_bad(float r) { return !(r > 0.f) || !isfinite(r); }
+
+template <typename S, bool kForce>
+__global__ void __launch_bounds__(32 * kTileY, 12) bulk16_kernel(const StepArgs p) {
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  const Lattice &L = p.L;
+  const int lane = threadIdx.x;
+  const int i = ti * kTileX + 4 * lane;  // the thread's nodes i .. i + 3
+  const int j = tj * kTileY + threadIdx.y;
+  // every lane loads from inside its row (clamped), so that the shuffles see
+  // all 32 lanes; results of clamped lanes are never stored.  Rows and planes
+  // start on 8-byte boundaries (the pitch is a multiple of 64 values).
+  const int ic = i < L.pitch - 4 ? i : L.pitch - 4;
+  const S *__restrict__ src = static_cast<const S *>(p.src);
+  uint32_t wa[9], wb[9];  // sources of nodes (i, i+1) and (i+2, i+3), packed
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      if (lo_ok) Store<S>::st(dst + (int64_t)a * L.plane, vlo(o[a]));
-      if (hi_ok) Store<S>::st(dst + (int64_t)a * L.plane + 1, vhi(o[a]));
+  for (int a = 0; a < 9; ++a) {
+    int r = j - cy_of(a);
+    r = r < 0 ? 0 : (r > L.ny - 1 ? L.ny - 1 : r);
+    const S *row = src + (int64_t)a * L.plane + (int64_t)r * L.pitch;
+    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(row + ic));
+    if (cx_of(a) == 0) {
+      wa[a] = w.x;
+      wb[a] = w.y;
+    } else if (cx_of(a) > 0) {  // sources i-1 (the left lane's last value) .. i+2
+      uint32_t left = __shfl_up_sync(0xffffffffu, w.y, 1);
+      if (lane == 0)
+        left = ic >= 1 ? ((uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic - 1)) << 16)
+                       : 0u;
+      wa[a] = shift16(left, w.x);
+      wb[a] = shift16(w.x, w.y);
+    } else {  // sources i+1 .. i+4 (the right lane's first value)
+      uint32_t right = __shfl_down_sync(0xffffffffu, w.x, 1);
+      if (lane == 31)
+        right = ic + 4 < L.pitch ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic + 4))
+                                 : 0u;
+      wa[a] = shift16(w.x, w.y);
+      wb[a] = shift16(w.y, right);
     }
   }
-  if ((lo_ok && (!(vlo(rho) > 0.f) || !isfinite(vlo(rho)))) ||
-      (hi_ok && (!(vhi(rho) > 0.f) || !isfinite(vhi(rho)))))
-    atomicOr(p.status, kStatusUnstable);
+  {
+    const ForceRegion reg = *p.reg_src;
+    if (ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1) return;  // special kernel
+  }
+  if (j < 1 || j > L.ny - 2) return;  // edge rows: special kernel
+  bool ok[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ok[k] = i + k >= 1 && i + k <= L.nx - 2;
+  if (!ok[0] && !ok[1] && !ok[2] && !ok[3]) return;
+  S *dst = static_cast<S *>(p.dst) + (int64_t)j * L.pitch + i;
+  // the two pairs one after the other, each stored as soon as it is done
+  bool bad = false;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t o[9];
+    const F2 r = collide_pair16<S, kForce>(p, half ? wb : wa, o);
+    const bool ok0 = ok[2 * half], ok1 = ok[2 * half + 1];
+    S *d2 = dst + 2 * half;
+    if (ok0 && ok1) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) *reinterpret_cast<uint32_t *>(d2 + (int64_t)a * L.plane) = o[a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        unsigned short *d = reinterpret_cast<unsigned short *>(d2 + (int64_t)a * L.plane);
+        if (ok0) d[0] = (unsigned short)(o[a] & 0xffffu);
+        if (ok1) d[1] = (unsigned short)(o[a] >> 16);
+      }
+    }
+    bad |= (ok0 && rho_bad(vlo(r))) || (ok1 && rho_bad(vhi(r)));
+  }
+  if (bad) atomicOr(p.status, kStatusUnstable);
 }
 
 template <typename S, bool kGather>
@@ -976,11 +1008,12 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(const StepArgs p) {
 template <typename S>
 cudaError_t bulk_t(const StepArgs &a, cudaStream_t s) {
   const dim3 grid(a.ntiles_x, a.ntiles_y);
-  if constexpr (sizeof(S) == 2) {  // two nodes per thread
+  if constexpr (sizeof(S) == 2) {  // four nodes per thread, one warp per tile row
+    static_assert(kTileX == 4 * 32, "bulk16_kernel maps a tile row onto one warp");
     if (a.L.has_bf)
-      bulk16_kernel<S, true><<<grid, dim3(kTileX / 2, kTileY), 0, s>>>(a);
+      bulk16_kernel<S, true><<<grid, dim3(32, kTileY), 0, s>>>(a);
     else
-      bulk16_kernel<S, false><<<grid, dim3(kTileX / 2, kTileY), 0, s>>>(a);
+      bulk16_kernel<S, false><<<grid, dim3(32, kTileY), 0, s>>>(a);
     return cudaGetLastError();
   }
   if (a.L.has_bf)
