@@ -843,17 +843,20 @@ __device__ __forceinline__ void collide2(const V (&h)[9], V drho, V dux, V duy, 
 }
 
 // ---------------------------------------------------------------------------
-// bulk kernel for 16-bit storage: four nodes per thread.  HBM stays busy
-// only with enough bytes in flight per SM; with 2-byte values and one node per
-// thread that needs more threads than the registers allow.  So each thread
-// takes the nodes i .. i+3 (i a multiple of 4) of a tile row, one warp per
-// row: one aligned 64-bit load per plane brings four values, kept packed (two
-// 32-bit words per plane, 18 registers for 4 nodes).  For c_x = +1 (sources
-// i-1 .. i+2) and c_x = -1 (sources i+1 .. i+4) the value beyond the thread's
-// four comes from the next lane by a warp shuffle (one extra 2-byte load at
-// the warp's edge) and a funnel shift realigns the words.  The nodes are
-// collided two at a time in packed f32x2 (collide2) and leave in one 64-bit
-// store per plane.
+// bulk kernel for 16-bit storage: eight nodes per thread.  HBM stays busy
+// only with enough bytes in flight per SM, and a thread holds what it loads
+// in registers until it is used; with 2-byte values the registers, not the
+// threads, cap what is in flight.  So each thread takes the nodes i .. i+7
+// (i a multiple of 8) of a tile row, a half-warp per row and one warp per
+// 128 x 2 tile: one aligned 128-bit load per plane brings eight values, kept
+// packed (four 32-bit words per plane, 36 registers for 8 nodes: 144 bytes
+// in flight per thread).  For c_x = +1 (sources i-1 .. i+6) and c_x = -1
+// (sources i+1 .. i+8) the value beyond the thread's eight comes from the
+// next lane of the half-warp by a shuffle (one extra 2-byte load at the
+// row's edge) and a funnel shift realigns the words.  The nodes are collided
+// two at a time in packed f32x2 (collide2) and leave in one 128-bit store per
+// plane.  96 registers, 20 one-warp blocks per SM: about 90 KB in flight per
+// SM.
 // ---------------------------------------------------------------------------
 template <typename S>
 struct Pair16;
@@ -921,41 +924,47 @@ __device__ __forceinline__ F2 collide_pair16(const StepArgs &p, const uint32_t (
 __device__ __forceinline__ bool rho_bad(float r) { return !(r > 0.f) || !isfinite(r); }
 
 template <typename S, bool kForce>
-__global__ void __launch_bounds__(32 * kTileY, 12) bulk16_kernel(const StepArgs p) {
+__global__ void __launch_bounds__(32, 20) bulk16_kernel(const StepArgs p) {
   const int ti = blockIdx.x, tj = blockIdx.y;
   const Lattice &L = p.L;
-  const int lane = threadIdx.x;
-  const int i = ti * kTileX + 4 * lane;  // the thread's nodes i .. i + 3
-  const int j = tj * kTileY + threadIdx.y;
+  const int lane = threadIdx.x & 15;               // lane within the tile row
+  const int i = ti * kTileX + 8 * lane;            // the thread's nodes i .. i + 7
+  const int j = tj * kTileY + (threadIdx.x >> 4);  // half-warp per tile row
   // every lane loads from inside its row (clamped), so that the shuffles see
-  // all 32 lanes; results of clamped lanes are never stored.  Rows and planes
-  // start on 8-byte boundaries (the pitch is a multiple of 64 values).
-  const int ic = i < L.pitch - 4 ? i : L.pitch - 4;
+  // all lanes; results of clamped lanes are never stored.  Rows and planes
+  // start on 16-byte boundaries (the pitch is a multiple of 64 values).
+  const int ic = i < L.pitch - 8 ? i : L.pitch - 8;
   const S *__restrict__ src = static_cast<const S *>(p.src);
-  uint32_t wa[9], wb[9];  // sources of nodes (i, i+1) and (i+2, i+3), packed
+  uint32_t w[4][9];  // sources of the node pairs (i, i+1) .. (i+6, i+7), packed
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     int r = j - cy_of(a);
     r = r < 0 ? 0 : (r > L.ny - 1 ? L.ny - 1 : r);
     const S *row = src + (int64_t)a * L.plane + (int64_t)r * L.pitch;
-    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(row + ic));
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row + ic));
     if (cx_of(a) == 0) {
-      wa[a] = w.x;
-      wb[a] = w.y;
-    } else if (cx_of(a) > 0) {  // sources i-1 (the left lane's last value) .. i+2
-      uint32_t left = __shfl_up_sync(0xffffffffu, w.y, 1);
+      w[0][a] = v.x;
+      w[1][a] = v.y;
+      w[2][a] = v.z;
+      w[3][a] = v.w;
+    } else if (cx_of(a) > 0) {  // sources i-1 (the left lane's last value) .. i+6
+      uint32_t left = __shfl_up_sync(0xffffffffu, v.w, 1, 16);
       if (lane == 0)
         left = ic >= 1 ? ((uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic - 1)) << 16)
                        : 0u;
-      wa[a] = shift16(left, w.x);
-      wb[a] = shift16(w.x, w.y);
-    } else {  // sources i+1 .. i+4 (the right lane's first value)
-      uint32_t right = __shfl_down_sync(0xffffffffu, w.x, 1);
-      if (lane == 31)
-        right = ic + 4 < L.pitch ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic + 4))
+      w[0][a] = shift16(left, v.x);
+      w[1][a] = shift16(v.x, v.y);
+      w[2][a] = shift16(v.y, v.z);
+      w[3][a] = shift16(v.z, v.w);
+    } else {  // sources i+1 .. i+8 (the right lane's first value)
+      uint32_t right = __shfl_down_sync(0xffffffffu, v.x, 1, 16);
+      if (lane == 15)
+        right = ic + 8 < L.pitch ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic + 8))
                                  : 0u;
-      wa[a] = shift16(w.x, w.y);
-      wb[a] = shift16(w.y, right);
+      w[0][a] = shift16(v.x, v.y);
+      w[1][a] = shift16(v.y, v.z);
+      w[2][a] = shift16(v.z, v.w);
+      w[3][a] = shift16(v.w, right);
     }
   }
   {
@@ -963,31 +972,32 @@ __global__ void __launch_bounds__(32 * kTileY, 12) bulk16_kernel(const StepArgs 
     if (ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1) return;  // special kernel
   }
   if (j < 1 || j > L.ny - 2) return;  // edge rows: special kernel
-  bool ok[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) ok[k] = i + k >= 1 && i + k <= L.nx - 2;
-  if (!ok[0] && !ok[1] && !ok[2] && !ok[3]) return;
-  S *dst = static_cast<S *>(p.dst) + (int64_t)j * L.pitch + i;
-  // the two pairs one after the other, each stored as soon as it is done
+  const int n_ok_lo = i >= 1 ? 0 : 1;                    // first node to store
+  const int n_ok_hi = L.nx - 2 - i < 7 ? L.nx - 2 - i : 7;  // last node to store
+  if (n_ok_hi < n_ok_lo) return;
+  uint32_t out[4][9];
   bool bad = false;
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    uint32_t o[9];
-    const F2 r = collide_pair16<S, kForce>(p, half ? wb : wa, o);
-    const bool ok0 = ok[2 * half], ok1 = ok[2 * half + 1];
-    S *d2 = dst + 2 * half;
-    if (ok0 && ok1) {
+  for (int k = 0; k < 4; ++k) {
+    const F2 r = collide_pair16<S, kForce>(p, w[k], out[k]);
+    bad |= (2 * k >= n_ok_lo && 2 * k <= n_ok_hi && rho_bad(vlo(r))) ||
+           (2 * k + 1 >= n_ok_lo && 2 * k + 1 <= n_ok_hi && rho_bad(vhi(r)));
+  }
+  S *dst = static_cast<S *>(p.dst) + (int64_t)j * L.pitch + i;
+  if (n_ok_lo == 0 && n_ok_hi == 7) {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) *reinterpret_cast<uint32_t *>(d2 + (int64_t)a * L.plane) = o[a];
-    } else {
+    for (int a = 0; a < 9; ++a)
+      *reinterpret_cast<uint4 *>(dst + (int64_t)a * L.plane) =
+          make_uint4(out[0][a], out[1][a], out[2][a], out[3][a]);
+  } else {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        unsigned short *d = reinterpret_cast<unsigned short *>(d2 + (int64_t)a * L.plane);
-        if (ok0) d[0] = (unsigned short)(o[a] & 0xffffu);
-        if (ok1) d[1] = (unsigned short)(o[a] >> 16);
-      }
+    for (int a = 0; a < 9; ++a) {
+      unsigned short *d = reinterpret_cast<unsigned short *>(dst + (int64_t)a * L.plane);
+#pragma unroll
+      for (int n = 0; n < 8; ++n)
+        if (n >= n_ok_lo && n <= n_ok_hi)
+          d[n] = (unsigned short)(n & 1 ? out[n >> 1][a] >> 16 : out[n >> 1][a] & 0xffffu);
     }
-    bad |= (ok0 && rho_bad(vlo(r))) || (ok1 && rho_bad(vhi(r)));
   }
   if (bad) atomicOr(p.status, kStatusUnstable);
 }
@@ -1008,12 +1018,12 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(const StepArgs p) {
 template <typename S>
 cudaError_t bulk_t(const StepArgs &a, cudaStream_t s) {
   const dim3 grid(a.ntiles_x, a.ntiles_y);
-  if constexpr (sizeof(S) == 2) {  // four nodes per thread, one warp per tile row
-    static_assert(kTileX == 4 * 32, "bulk16_kernel maps a tile row onto one warp");
+  if constexpr (sizeof(S) == 2) {  // eight nodes per thread, one warp per tile
+    static_assert(kTileX == 8 * 16 && kTileY == 2, "bulk16_kernel maps a tile onto one warp");
     if (a.L.has_bf)
-      bulk16_kernel<S, true><<<grid, dim3(32, kTileY), 0, s>>>(a);
+      bulk16_kernel<S, true><<<grid, dim3(32), 0, s>>>(a);
     else
-      bulk16_kernel<S, false><<<grid, dim3(32, kTileY), 0, s>>>(a);
+      bulk16_kernel<S, false><<<grid, dim3(32), 0, s>>>(a);
     return cudaGetLastError();
   }
   if (a.L.has_bf)
