@@ -240,6 +240,30 @@ vplbm_status vplbm_check(vplbm_ctx *ctx);
 /* Number of kernels the library has launched on this lattice so far. */
 vplbm_status vplbm_launch_count(vplbm_ctx *ctx, int64_t *n);
 
+/* ---- launch forms of the bulk kernel and their tuner ----
+ * No counterpart in the paper.  The kernel that updates every node away
+ * from the edges and the body comes in three launch forms which compute the
+ * same values bit for bit: FP32/FP64 storage, blocks of one, two or four
+ * 128 x 2 tiles; 16-bit storage, eight nodes per thread at 96 or 126
+ * registers, or four nodes per thread.  Form 0 is the default.
+ *
+ * vplbm_autotune times the forms on this lattice's own steps: three passes
+ * over the forms, each form running 32 untimed steps (its step graph is
+ * captured there) and then `trials` steps timed with CUDA events on the
+ * lattice's stream (1 <= trials <= 10000); each form's fastest pass counts.
+ * It keeps the fastest form and writes its index to *variant (may be NULL).
+ * The lattice advances by 9 * (32 + trials) steps, which give the same state,
+ * histories and sums as vplbm_step of that count (the forms agree bit for
+ * bit).  Synchronises the stream.  ESTATE before vplbm_set_body.  Step graphs
+ * are rebuilt after a change of form; batches re-capture theirs at their
+ * next step.
+ *
+ * vplbm_set_bulk_variant selects a form (0 .. 2, else EINVAL);
+ * vplbm_bulk_variant reads the current one. */
+vplbm_status vplbm_autotune(vplbm_ctx *ctx, int32_t trials, int32_t *variant);
+vplbm_status vplbm_set_bulk_variant(vplbm_ctx *ctx, int32_t variant);
+vplbm_status vplbm_bulk_variant(vplbm_ctx *ctx, int32_t *variant);
+
 /* ---- batches: several lattices stepped together ----
  * A batch steps n independent lattices (any sizes and storage types, one
  * device).  The lattices share no data, so each runs its steps on a stream of
@@ -272,6 +296,13 @@ vplbm_status vplbm_batch_create(vplbm_ctx *const *ctxs, int32_t n, void *cuda_st
  * (nothing is queued then).  A vplbm_set_body on a member between calls is
  * seen by the next call. */
 vplbm_status vplbm_batch_step(vplbm_batch *batch, int32_t nsteps);
+
+/* The bulk kernel's launch form for every lattice of the batch, timed on the
+ * batch's own steps as vplbm_autotune does for one lattice (the same form on
+ * every lattice, 9 * (32 + trials) batch steps, events on the batch's
+ * stream).  The fastest form is set on every lattice and written to *variant
+ * (may be NULL).  ESTATE when a lattice has no body placed. */
+vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int32_t trials, int32_t *variant);
 
 /* Releases the batch (never its contexts).  NULL is accepted. */
 void vplbm_batch_destroy(vplbm_batch *batch);

@@ -236,6 +236,7 @@ struct vplbm_ctx {
   cudaStream_t side = nullptr;      // the special kernel's stream
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int region_slots = 1;             // blocks reserved for force-region tiles
+  int bulk_variant = 0;             // launch form of the bulk kernel (kBulkVariants)
   double sim_const[3] = {0.0, 0.0, 0.0};  // -(1/3) sum S n and its moment
   std::string err;
   double s_plus, s_minus, a_plus, a_minus, half_pen;
@@ -359,7 +360,7 @@ cudaError_t queue_step(vplbm_ctx *c, cudaStream_t s, int src, bool pre, bool do_
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
   if (e == cudaSuccess) e = launch_special(c->cfg.dtype, true, a, c->side);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
-  if (e == cudaSuccess) e = launch_bulk(c->cfg.dtype, a, s);
+  if (e == cudaSuccess) e = launch_bulk(c->cfg.dtype, c->bulk_variant, a, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
   c->launches += 2;
   c->pending = a.defer != 0;
@@ -412,6 +413,38 @@ vplbm_status sync(vplbm_ctx *c) {
 vplbm_status read_status(vplbm_ctx *c, int32_t *st) {
   VPLBM_CUDA(c, cudaMemcpyAsync(st, c->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   return sync(c);
+}
+
+constexpr int kTuneRounds = 3;
+
+void set_variant(vplbm_ctx *c, int v) {
+  if (v == c->bulk_variant) return;
+  c->bulk_variant = v;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  ++c->generation;  // batches re-capture their graphs
+}
+
+// Elapsed milliseconds of the work `queue` puts on stream s, per step.
+template <typename F>
+vplbm_status timed(cudaStream_t s, int steps, float *ms, F queue, vplbm_ctx *c) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  vplbm_status st = VPLBM_OK;
+  if (e == cudaSuccess) st = queue();
+  if (e == cudaSuccess && st == VPLBM_OK) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess && st == VPLBM_OK) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess && st == VPLBM_OK) e = cudaEventElapsedTime(ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st != VPLBM_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(c, e, "timing a launch form");
+  *ms /= (float)steps;
+  return VPLBM_OK;
 }
 
 }  // namespace
@@ -900,6 +933,44 @@ vplbm_status vplbm_launch_count(vplbm_ctx *c, int64_t *n) {
   return VPLBM_OK;
 }
 
+vplbm_status vplbm_autotune(vplbm_ctx *c, int32_t trials, int32_t *variant) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (trials < 1 || trials > 10000) return fail(c, VPLBM_EINVAL, "trials must be in 1 .. 10000");
+  if (!c->has_body) return fail(c, VPLBM_ESTATE, "place a body first");
+  // the forms in turn, kTuneRounds times: per form 2 * kGraphPairs untimed
+  // steps (the step graph is captured there), then `trials` timed steps;
+  // each form's fastest round counts
+  float t[kBulkVariants];
+  for (int r = 0; r < kTuneRounds; ++r)
+    for (int v = 0; v < kBulkVariants; ++v) {
+      set_variant(c, v);
+      if (vplbm_status st = vplbm_step(c, 2 * kGraphPairs)) return st;
+      float ms = 0.f;
+      if (vplbm_status st = timed(c->stream, trials, &ms, [&] { return vplbm_step(c, trials); }, c))
+        return st;
+      t[v] = r == 0 ? ms : std::min(t[v], ms);
+    }
+  int best = 0;
+  for (int v = 1; v < kBulkVariants; ++v)
+    if (t[v] < t[best]) best = v;
+  set_variant(c, best);
+  if (variant) *variant = best;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_set_bulk_variant(vplbm_ctx *c, int32_t variant) {
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (variant < 0 || variant >= kBulkVariants) return fail(c, VPLBM_EINVAL, "no such variant");
+  set_variant(c, variant);
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_bulk_variant(vplbm_ctx *c, int32_t *variant) {
+  if (!c || !variant) return fail(c, VPLBM_EINVAL, "NULL argument");
+  *variant = c->bulk_variant;
+  return VPLBM_OK;
+}
+
 void vplbm_destroy(vplbm_ctx *c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -1072,6 +1143,29 @@ vplbm_status vplbm_batch_create(vplbm_ctx *const *ctxs, int32_t n, void *cuda_st
     return batch_cuda(e, "vplbm_batch_create: cudaEventCreateWithFlags");
   }
   *out = b;
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_batch_autotune(vplbm_batch *b, int32_t trials, int32_t *variant) {
+  if (!b) return batch_fail(VPLBM_EINVAL, "vplbm_batch_autotune: batch is NULL");
+  if (trials < 1 || trials > 10000)
+    return batch_fail(VPLBM_EINVAL, "vplbm_batch_autotune: trials must be in 1 .. 10000");
+  float t[kBulkVariants];
+  for (int r = 0; r < kTuneRounds; ++r)
+    for (int v = 0; v < kBulkVariants; ++v) {
+      for (vplbm_ctx *c : b->ctxs) set_variant(c, v);
+      if (vplbm_status st = vplbm_batch_step(b, 2 * kGraphPairs)) return st;
+      float ms = 0.f;
+      if (vplbm_status st = timed(b->stream, trials, &ms, [&] { return vplbm_batch_step(b, trials); },
+                                  nullptr))
+        return st;
+      t[v] = r == 0 ? ms : std::min(t[v], ms);
+    }
+  int best = 0;
+  for (int v = 1; v < kBulkVariants; ++v)
+    if (t[v] < t[best]) best = v;
+  for (vplbm_ctx *c : b->ctxs) set_variant(c, best);
+  if (variant) *variant = best;
   return VPLBM_OK;
 }
 

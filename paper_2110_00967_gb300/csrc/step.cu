@@ -670,13 +670,14 @@ __global__ void __launch_bounds__(kThreads) special_kernel(const StepArgs p) {
 // bulk kernel: every node off the lattice edges and outside the force-region
 // tiles -- fluid nodes whose pull sources all lie inside the lattice.
 // ---------------------------------------------------------------------------
-template <typename S, bool kForce>
-__global__ void __launch_bounds__(kThreads) bulk_kernel(const StepArgs p) {
+template <typename S, bool kForce, int kTiles>
+__global__ void __launch_bounds__(kThreads * kTiles) bulk_kernel(const StepArgs p) {
   using T = typename Store<S>::T;
-  const int ti = blockIdx.x, tj = blockIdx.y;
   const Lattice &L = p.L;
+  const int ti = blockIdx.x;
   const int i = ti * kTileX + threadIdx.x;
-  const int j = tj * kTileY + threadIdx.y;
+  const int j = blockIdx.y * (kTileY * kTiles) + threadIdx.y;  // a block is kTiles tiles high
+  const int tj = j / kTileY;
   if (i < 1 || i > L.nx - 2 || j < 1 || j > L.ny - 2) return;  // edge nodes: special kernel
   const S *__restrict__ src = static_cast<const S *>(p.src);
   S *__restrict__ dst = static_cast<S *>(p.dst);
@@ -923,8 +924,8 @@ __device__ __forceinline__ F2 collide_pair16(const StepArgs &p, const uint32_t (
 
 __device__ __forceinline__ bool rho_bad(float r) { return !(r > 0.f) || !isfinite(r); }
 
-template <typename S, bool kForce>
-__global__ void __launch_bounds__(32, 20) bulk16_kernel(const StepArgs p) {
+template <typename S, bool kForce, int kMinBlocks>
+__global__ void __launch_bounds__(32, kMinBlocks) bulk16_kernel(const StepArgs p) {
   const int ti = blockIdx.x, tj = blockIdx.y;
   const Lattice &L = p.L;
   const int lane = threadIdx.x & 15;               // lane within the tile row
@@ -1002,6 +1003,80 @@ __global__ void __launch_bounds__(32, 20) bulk16_kernel(const StepArgs p) {
   if (bad) atomicOr(p.status, kStatusUnstable);
 }
 
+// The same update with four nodes per thread (one 64-bit load per plane, one
+// warp per tile row, 80 registers): a variant for the tuner.
+template <typename S, bool kForce>
+__global__ void __launch_bounds__(32 * kTileY, 12) bulk16x4_kernel(const StepArgs p) {
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  const Lattice &L = p.L;
+  const int lane = threadIdx.x;
+  const int i = ti * kTileX + 4 * lane;  // the thread's nodes i .. i + 3
+  const int j = tj * kTileY + threadIdx.y;
+  // every lane loads from inside its row (clamped), so that the shuffles see
+  // all 32 lanes; results of clamped lanes are never stored.  Rows and planes
+  // start on 8-byte boundaries (the pitch is a multiple of 64 values).
+  const int ic = i < L.pitch - 4 ? i : L.pitch - 4;
+  const S *__restrict__ src = static_cast<const S *>(p.src);
+  uint32_t wa[9], wb[9];  // sources of nodes (i, i+1) and (i+2, i+3), packed
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    int r = j - cy_of(a);
+    r = r < 0 ? 0 : (r > L.ny - 1 ? L.ny - 1 : r);
+    const S *row = src + (int64_t)a * L.plane + (int64_t)r * L.pitch;
+    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(row + ic));
+    if (cx_of(a) == 0) {
+      wa[a] = w.x;
+      wb[a] = w.y;
+    } else if (cx_of(a) > 0) {  // sources i-1 (the left lane's last value) .. i+2
+      uint32_t left = __shfl_up_sync(0xffffffffu, w.y, 1);
+      if (lane == 0)
+        left = ic >= 1 ? ((uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic - 1)) << 16)
+                       : 0u;
+      wa[a] = shift16(left, w.x);
+      wb[a] = shift16(w.x, w.y);
+    } else {  // sources i+1 .. i+4 (the right lane's first value)
+      uint32_t right = __shfl_down_sync(0xffffffffu, w.x, 1);
+      if (lane == 31)
+        right = ic + 4 < L.pitch ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(row + ic + 4))
+                                 : 0u;
+      wa[a] = shift16(w.x, w.y);
+      wb[a] = shift16(w.y, right);
+    }
+  }
+  {
+    const ForceRegion reg = *p.reg_src;
+    if (ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1) return;  // special kernel
+  }
+  if (j < 1 || j > L.ny - 2) return;  // edge rows: special kernel
+  bool ok[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ok[k] = i + k >= 1 && i + k <= L.nx - 2;
+  if (!ok[0] && !ok[1] && !ok[2] && !ok[3]) return;
+  S *dst = static_cast<S *>(p.dst) + (int64_t)j * L.pitch + i;
+  // the two pairs one after the other, each stored as soon as it is done
+  bool bad = false;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t o[9];
+    const F2 r = collide_pair16<S, kForce>(p, half ? wb : wa, o);
+    const bool ok0 = ok[2 * half], ok1 = ok[2 * half + 1];
+    S *d2 = dst + 2 * half;
+    if (ok0 && ok1) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) *reinterpret_cast<uint32_t *>(d2 + (int64_t)a * L.plane) = o[a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        unsigned short *d = reinterpret_cast<unsigned short *>(d2 + (int64_t)a * L.plane);
+        if (ok0) d[0] = (unsigned short)(o[a] & 0xffffu);
+        if (ok1) d[1] = (unsigned short)(o[a] >> 16);
+      }
+    }
+    bad |= (ok0 && rho_bad(vlo(r))) || (ok1 && rho_bad(vhi(r)));
+  }
+  if (bad) atomicOr(p.status, kStatusUnstable);
+}
+
 template <typename S, bool kGather>
 cudaError_t special_t(const StepArgs &a, cudaStream_t s) {
   const int tiles = a.all_tiles ? a.ntiles_x * a.ntiles_y : a.edge_blocks + a.region_slots;
@@ -1015,22 +1090,31 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(const StepArgs p) {
   finalize<T>(p, p.acc_prev);
 }
 
-template <typename S>
-cudaError_t bulk_t(const StepArgs &a, cudaStream_t s) {
-  const dim3 grid(a.ntiles_x, a.ntiles_y);
-  if constexpr (sizeof(S) == 2) {  // eight nodes per thread, one warp per tile
+template <typename S, bool kForce>
+cudaError_t bulk_v(int variant, const StepArgs &a, cudaStream_t s) {
+  if constexpr (sizeof(S) == 2) {
     static_assert(kTileX == 8 * 16 && kTileY == 2, "bulk16_kernel maps a tile onto one warp");
-    if (a.L.has_bf)
-      bulk16_kernel<S, true><<<grid, dim3(32), 0, s>>>(a);
-    else
-      bulk16_kernel<S, false><<<grid, dim3(32), 0, s>>>(a);
-    return cudaGetLastError();
+    const dim3 grid(a.ntiles_x, a.ntiles_y);
+    switch (variant) {
+      case 0: bulk16_kernel<S, kForce, 20><<<grid, dim3(32), 0, s>>>(a); break;  // 8 nodes, 96 regs
+      case 1: bulk16_kernel<S, kForce, 16><<<grid, dim3(32), 0, s>>>(a); break;  // 8 nodes, 126 regs
+      case 2: bulk16x4_kernel<S, kForce><<<grid, dim3(32, kTileY), 0, s>>>(a); break;  // 4 nodes
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    const int k = variant == 0 ? 1 : (variant == 1 ? 2 : 4);  // tiles per block
+    if (variant < 0 || variant > 2) return cudaErrorInvalidValue;
+    const dim3 grid(a.ntiles_x, (a.ntiles_y + k - 1) / k), block(kTileX, kTileY * k);
+    if (k == 1) bulk_kernel<S, kForce, 1><<<grid, block, 0, s>>>(a);
+    else if (k == 2) bulk_kernel<S, kForce, 2><<<grid, block, 0, s>>>(a);
+    else bulk_kernel<S, kForce, 4><<<grid, block, 0, s>>>(a);
   }
-  if (a.L.has_bf)
-    bulk_kernel<S, true><<<grid, dim3(kTileX, kTileY), 0, s>>>(a);
-  else
-    bulk_kernel<S, false><<<grid, dim3(kTileX, kTileY), 0, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t bulk_t(int variant, const StepArgs &a, cudaStream_t s) {
+  return a.L.has_bf ? bulk_v<S, true>(variant, a, s) : bulk_v<S, false>(variant, a, s);
 }
 
 }  // namespace
@@ -1054,12 +1138,12 @@ cudaError_t launch_finalize(int dtype, const StepArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_bulk(int dtype, const StepArgs &a, cudaStream_t s) {
+cudaError_t launch_bulk(int dtype, int variant, const StepArgs &a, cudaStream_t s) {
   switch (dtype) {
-    case VPLBM_F64: return bulk_t<double>(a, s);
-    case VPLBM_F32: return bulk_t<float>(a, s);
-    case VPLBM_F16_OFS: return bulk_t<__half>(a, s);
-    case VPLBM_BF16_OFS: return bulk_t<__nv_bfloat16>(a, s);
+    case VPLBM_F64: return bulk_t<double>(variant, a, s);
+    case VPLBM_F32: return bulk_t<float>(variant, a, s);
+    case VPLBM_F16_OFS: return bulk_t<__half>(variant, a, s);
+    case VPLBM_BF16_OFS: return bulk_t<__nv_bfloat16>(variant, a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -537,7 +537,11 @@ cudaError_t launch_special(int dtype, bool gather, const StepArgs &a, cudaStream
 // row, running sums, step counter
 cudaError_t launch_finalize(int dtype, const StepArgs &a, cudaStream_t s);
 // the bulk kernel: the nodes off the edges, outside the force-region tiles
-cudaError_t launch_bulk(int dtype, const StepArgs &a, cudaStream_t s);
+// the bulk kernel in one of kBulkVariants launch forms (same results, bit
+// for bit): FP32 and FP64 blocks of 1, 2 or 4 tiles; 16-bit storage with
+// eight nodes per thread at 96 or 126 registers, or four nodes per thread
+constexpr int kBulkVariants = 3;
+cudaError_t launch_bulk(int dtype, int variant, const StepArgs &a, cudaStream_t s);
 
 // auxiliary kernels (aux.cu)
 cudaError_t launch_raster(const Lattice &L, const BodyState *body, uint8_t *chi, int i0, int j0,

@@ -110,8 +110,12 @@ _SIGS = [
     ("vplbm_get_sim_nodes", [_vp, _P(C.c_int32), C.c_int32, _P(C.c_int32)], C.c_int),
     ("vplbm_check", [_vp], C.c_int),
     ("vplbm_launch_count", [_vp, _P(C.c_int64)], C.c_int),
+    ("vplbm_autotune", [_vp, C.c_int32, _P(C.c_int32)], C.c_int),
+    ("vplbm_set_bulk_variant", [_vp, C.c_int32], C.c_int),
+    ("vplbm_bulk_variant", [_vp, _P(C.c_int32)], C.c_int),
     ("vplbm_batch_create", [_P(_vp), C.c_int32, _vp, _P(_vp)], C.c_int),
     ("vplbm_batch_step", [_vp, C.c_int32], C.c_int),
+    ("vplbm_batch_autotune", [_vp, C.c_int32, _P(C.c_int32)], C.c_int),
     ("vplbm_batch_destroy", [_vp], None),
     ("vplbm_sim_force_static", [_P(vplbm_config), _vp, _vp, C.c_int32, _P(C.c_double),
                                 _P(C.c_double), _P(C.c_double), _vp], C.c_int),
@@ -266,6 +270,22 @@ def vplbm_launch_count(ctx) -> int:
     return n.value
 
 
+def vplbm_autotune(ctx, trials: int = 20) -> int:
+    v = C.c_int32()
+    _check(lib().vplbm_autotune(ctx, trials, C.byref(v)), ctx)
+    return v.value
+
+
+def vplbm_set_bulk_variant(ctx, variant: int):
+    _check(lib().vplbm_set_bulk_variant(ctx, variant), ctx)
+
+
+def vplbm_bulk_variant(ctx) -> int:
+    v = C.c_int32()
+    _check(lib().vplbm_bulk_variant(ctx, C.byref(v)), ctx)
+    return v.value
+
+
 def vplbm_batch_create(ctxs, stream: int):
     arr = (_vp * len(ctxs))(*ctxs)
     b = _vp()
@@ -275,6 +295,12 @@ def vplbm_batch_create(ctxs, stream: int):
 
 def vplbm_batch_step(batch, nsteps: int):
     _check(lib().vplbm_batch_step(batch, nsteps))
+
+
+def vplbm_batch_autotune(batch, trials: int = 20) -> int:
+    v = C.c_int32()
+    _check(lib().vplbm_batch_autotune(batch, trials, C.byref(v)))
+    return v.value
 
 
 def vplbm_batch_destroy(batch):
@@ -412,6 +438,17 @@ class Lattice:
     def launches(self) -> int:
         return vplbm_launch_count(self.ctx)
 
+    def autotune(self, trials: int = 20) -> int:
+        return vplbm_autotune(self.ctx, trials)
+
+    @property
+    def bulk_variant(self) -> int:
+        return vplbm_bulk_variant(self.ctx)
+
+    @bulk_variant.setter
+    def bulk_variant(self, v: int):
+        vplbm_set_bulk_variant(self.ctx, v)
+
 
 # ---------------------------------------------------------------------------
 # workloads -> ABI structures
@@ -461,6 +498,9 @@ class Batch:
 
     def step(self, n: int = 1):
         vplbm_batch_step(self.handle, n)
+
+    def autotune(self, trials: int = 20) -> int:
+        return vplbm_batch_autotune(self.handle, trials)
 
     @property
     def launches(self) -> int:

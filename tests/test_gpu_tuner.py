@@ -1,0 +1,119 @@
+"""The bulk kernel's launch forms and their tuner, through the C ABI: every
+form gives the same populations bit for bit (storage forms, ragged lattice
+sizes, with and without a body force), the tuner leaves the solution
+unchanged, remembers its choice per lattice shape, and rejects bad input."""
+import numpy as np
+import pytest
+
+from paper_2110_00967_gb300 import vplbm as V
+from paper_2110_00967_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+N_VARIANTS = 3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "the GPU tests need a CUDA device"
+    V.lib()
+    yield
+
+
+def lattice(w, variant=None, **over):
+    lat = V.Lattice(V.config_of(w, **over))
+    lat.set_body(V.body_of(w))
+    if variant is not None:
+        lat.bulk_variant = variant
+    return lat
+
+
+def ragged_naca(dtype, body_force=(0.0, 0.0)):
+    # 300 x 131: a ragged last tile column and row counts that are not
+    # multiples of the 2-, 4- and 8-row blocks
+    w = W.naca(8.0, dtype=dtype, nx=300, ny=131, chord=40.0)
+    return w.with_(body_force=body_force)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("force", [False, True])
+def test_every_form_gives_the_same_populations(dtype, force):
+    w = ragged_naca(dtype, body_force=(1e-6, -2e-6) if force else (0.0, 0.0))
+    ref = None
+    for v in range(N_VARIANTS):
+        lat = lattice(w, variant=v)
+        assert lat.bulk_variant == v
+        lat.step(70)  # two 32-step graphs and single steps
+        lat.check()
+        f = lat.get_f()
+        if ref is None:
+            ref = f
+        else:
+            assert np.array_equal(f, ref), f"form {v} differs from form 0"
+
+
+def tuning_steps(trials):
+    """Steps a tuner call advances: three passes over the forms, each form 32
+    untimed steps (one step graph) and `trials` timed ones."""
+    return 3 * N_VARIANTS * (32 + trials)
+
+
+def test_tuner_steps_are_ordinary_steps():
+    """A lattice tuned between steps ends bit-identical (populations and the
+    force histories) to one stepped the same number of steps; a batch stepped
+    after a change of a member's form matches single steps."""
+    w = W.naca(10.0, dtype="f16", nx=512, ny=256)
+    tuned = lattice(w)
+    tuned.step(20)
+    v = tuned.autotune(4)
+    assert 0 <= v < N_VARIANTS and tuned.bulk_variant == v
+    tuned.step(20)
+    n = 40 + tuning_steps(4)
+    assert tuned.steps == n
+    plain = lattice(w)
+    plain.step(n)
+    assert np.array_equal(tuned.get_f(), plain.get_f())
+    np.testing.assert_array_equal(tuned.history(V.MEM, 40), plain.history(V.MEM, 40))
+    np.testing.assert_array_equal(tuned.history(V.SIM, 40), plain.history(V.SIM, 40))
+    ref = lattice(w)
+    ref.step(40)
+    a, b = lattice(w), lattice(w)
+    batch = V.Batch([a, b])
+    batch.step(10)
+    a.bulk_variant = (a.bulk_variant + 1) % N_VARIANTS
+    batch.step(30)
+    batch.close()
+    assert np.array_equal(a.get_f(), ref.get_f())
+    assert np.array_equal(b.get_f(), ref.get_f())
+
+
+def test_batch_tuner_steps_are_ordinary_steps():
+    w = W.naca(5.0, dtype="bf16", nx=384, ny=192)
+    lats = [lattice(w) for _ in range(3)]
+    batch = V.Batch(lats)
+    batch.step(10)
+    v = batch.autotune(2)
+    assert 0 <= v < N_VARIANTS and all(l.bulk_variant == v for l in lats)
+    batch.step(20)
+    batch.close()
+    plain = lattice(w)
+    plain.step(30 + tuning_steps(2))
+    for l in lats:
+        assert np.array_equal(l.get_f(), plain.get_f())
+
+
+def test_tuner_rejects_bad_input():
+    w = W.naca(0.0, dtype="f32", nx=256, ny=128)
+    lat = V.Lattice(V.config_of(w))
+    with pytest.raises(V.VplbmError) as e:
+        lat.autotune(5)
+    assert e.value.status == V.ESTATE
+    lat.set_body(V.body_of(w))
+    for bad in (-1, N_VARIANTS):
+        with pytest.raises(V.VplbmError) as e:
+            lat.bulk_variant = bad
+        assert e.value.status == V.EINVAL
+    with pytest.raises(V.VplbmError) as e:
+        lat.autotune(0)
+    assert e.value.status == V.EINVAL
