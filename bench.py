@@ -470,6 +470,67 @@ def run_serving(args, rank, world, local_rank):
     }
 
 
+def run_naca_large(args, rank, world, local_rank):
+    """One 8192 x 4096 NACA 0012 lattice (C = 800, Re 1000: tau+ = 0.62; 2.4 GB
+    of FP32 populations, 1.2 GB in 16-bit storage), far larger than L2: the
+    bandwidth of a single lattice's step without the help of neighbouring
+    lattices running beside it.  Graph-replayed steps timed with events."""
+    import torch
+    from paper_2110_00967_gb300 import vplbm as V
+    from paper_2110_00967_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    w = W.naca(10.0, dtype=args.dtype, nx=8192, ny=4096, tau_plus=0.62)
+    lat = V.Lattice(V.config_of(w), device=dev, stream=stream)
+    lat.set_body(V.body_of(w))
+    variant = lat.autotune(32)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = lat.launches
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    start.record(stream)
+    lat.step(args.steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    barrier(world)
+    lat.check()
+    elapsed_ms = reduce_max(start.elapsed_time(end), world, dev)
+    nodes = w.nx * w.ny
+    bpl = BYTES_PER_LUP[args.dtype]
+    step_ms = elapsed_ms / args.steps
+    achieved = bpl * nodes / (step_ms / 1e3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": round(world * nodes * args.steps / (elapsed_ms / 1e3) / 1e6, 1),
+        "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(step_ms, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"naca0012-8192x4096-{args.dtype}-alpha10", "grid": [w.nx, w.ny],
+                   "instances": 1, "chord": 800, "reynolds": 1000, "tau_plus": 0.62,
+                   "storage": args.dtype, "bulk_variant": [variant],
+                   "l2": f"inputs larger than L2: {2 * bpl * nodes / 2 / 1e9:.1f} GB ping-pong",
+                   "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "one lattice step (bulk + special), timed over the region",
+                     "kernel_avg_us": round(step_ms * 1e3, 3), "bytes_per_lup": bpl,
+                     "peak_kind": peak_kind},
+        "gpu_launches": lat.launches - l0,
+        "clocks": clk,
+    }
+
+
 def run_disk(args, rank, world, local_rank):
     """The 256 x 128 FP64 disk channel (BGK tau 0.65, Re 20, MEM and SIM every
     step), 2000 steps from rest graph-replayed, timed whole; the FP64 oracle's
@@ -655,7 +716,7 @@ def main(argv=None):
                          "of the whole region)")
     ap.add_argument("--workload",
                     choices=("naca", "sedimentation", "serving", "disk", "naca-paper",
-                             "sedimentation-paper", "sim-variants"),
+                             "sedimentation-paper", "sim-variants", "naca-large"),
                     default="naca",
                     help="naca: the five NACA 0012 lattices (the benchmark); sedimentation: "
                          "the 400 x 1600 falling-disk box, MEM and SIM runs; serving: a seeded "
@@ -664,7 +725,7 @@ def main(argv=None):
                          "sedimentation-paper: the paper's D = 26 channel, four density "
                          "ratios, MEM and SIM (20,280 steps per physical second); sim-variants: "
                          "the paper's NACA case at 12 degrees once per SIM point count and "
-                         "order")
+                         "order; naca-large: one 8192 x 4096 lattice")
     ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
     ap.add_argument("--cap", type=int, default=20000, help="serving: step cap per request")
     ap.add_argument("--memory-gb", type=int, default=40, help="serving: device-memory budget")
@@ -695,6 +756,8 @@ def main(argv=None):
             line = run_serving(args, rank, world, local_rank)
         elif args.workload == "disk":
             line = run_disk(args, rank, world, local_rank)
+        elif args.workload == "naca-large":
+            line = run_naca_large(args, rank, world, local_rank)
         elif args.workload in ("naca-paper", "sim-variants"):
             line = run_naca_paper(args, rank, world, local_rank,
                                   sim_variants=args.workload == "sim-variants")
