@@ -582,8 +582,14 @@ __device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bo
 // special kernel: SIM blocks, then blocks of edge nodes, then the
 // force-region tiles (or, for the first step, every tile)
 // ---------------------------------------------------------------------------
+// With 16-bit storage the special kernels of lattices stepped side by side
+// share the SMs with a register-hungry bulk kernel: cap the special kernel at
+// 64 registers (four blocks per SM), which it meets without spilling.
+template <typename S>
+constexpr int kSpecialMinBlocks = sizeof(S) == 2 ? 4 : 1;
+
 template <typename S, bool kGather>
-__global__ void __launch_bounds__(kThreads) special_kernel(const StepArgs p) {
+__global__ void __launch_bounds__(kThreads, kSpecialMinBlocks<S>) special_kernel(const StepArgs p) {
   using T = typename Store<S>::T;
   __shared__ int is_last;
   const Lattice &L = p.L;
