@@ -598,8 +598,9 @@ SIM_VARIANTS = ((107, 0), (213, 0), (425, 0), (849, 0), (1697, 0), (3393, 0), (8
 
 def run_naca_paper(args, rank, world, local_rank, sim_variants=False):
     """The paper's own NACA 0012 case (C = 278, U0 = 0.0599, tau 0.55, 3614 x
-    1946 FP32) at the angles 0, 4, ..., 28 degrees as one batch; reports the
-    MLUPS of the timed steps and the Cd/Cl means over them (MEM and SIM).
+    1946 FP32) at ten angles from 0 to 28 degrees as one batch; reports the
+    MLUPS of the timed steps, the Cd/Cl means over them (MEM and SIM) and the
+    spread of Cl and Cd over the last (up to 50,000) of them.
     With `sim_variants`, the same case at 12 degrees once per SIM variant
     (point counts 107 .. 3393, stress copied or extrapolated to first order):
     the body is fixed, so every lattice carries the same flow and only the
@@ -621,7 +622,8 @@ def run_naca_paper(args, rank, world, local_rank, sim_variants=False):
                 for w, (_, order) in zip(works, SIM_VARIANTS)]
     else:
         works = [W.naca_paper(a, dtype=args.dtype) for a in W.PAPER_ANGLES]
-        lats = [V.Lattice(V.config_of(w), device=dev) for w in works]
+        lats = [V.Lattice(V.config_of(w, history_len=min(args.steps, 50_000)), device=dev)
+                for w in works]
     for w, lat in zip(works, lats):
         lat.set_body(V.body_of(w))
     batch = V.Batch(lats, stream=stream)
@@ -649,6 +651,15 @@ def run_naca_paper(args, rank, world, local_rank, sim_variants=False):
         coeffs[key] = {
             "cd_mem": sums[0] / n[0] / q, "cl_mem": sums[1] / n[0] / q,
             "cd_sim": sums[3] / n[1] / q, "cl_sim": sums[4] / n[1] / q}
+        if not sim_variants:
+            # unsteadiness over the last steps of the window (up to 50,000): the
+            # standard deviation and range of Cl and Cd per estimator
+            m = min(args.steps, 50_000)
+            for est, name in ((V.MEM, "mem"), (V.SIM, "sim")):
+                h = lat.history(est, m)
+                coeffs[key][f"cl_{name}_std"] = float(h[:, 1].std() / q)
+                coeffs[key][f"cd_{name}_std"] = float(h[:, 0].std() / q)
+                coeffs[key][f"cl_{name}_range"] = [float(h[:, 1].min() / q), float(h[:, 1].max() / q)]
     if sim_variants:
         ref = coeffs["n3393-order0"]
         for c in coeffs.values():
@@ -670,7 +681,7 @@ def run_naca_paper(args, rank, world, local_rank, sim_variants=False):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": (f"naca0012-paper-3614x1946-{args.dtype}-alpha12-sim-variants"
                                 if sim_variants else
-                                f"naca0012-paper-3614x1946-{args.dtype}-alpha0..28"),
+                                f"naca0012-paper-3614x1946-{args.dtype}-alpha0..28-10angles"),
                    "grid": [works[0].nx, works[0].ny], "instances": len(lats), "chord": 278,
                    "u0": 0.0599, "tau_plus": 0.55, "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

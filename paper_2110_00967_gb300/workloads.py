@@ -116,7 +116,9 @@ def naca_paper(alpha_deg: float = 0.0, dtype: str = "f32", steps: int = 200_000)
                 u0=0.0599, tau_plus=0.55)
 
 
-PAPER_ANGLES = (0.0, 4.0, 8.0, 12.0, 16.0, 20.0, 24.0, 28.0)
+# angles of attack of the paper's sweep (Sec. 3.1: 0 to 28 degrees; 7, 10, 24
+# and 26 are the angles it discusses, 26 the stall)
+PAPER_ANGLES = (0.0, 4.0, 7.0, 10.0, 12.0, 16.0, 20.0, 24.0, 26.0, 28.0)
 
 
 # kinematic viscosity of the sedimentation cases (Sec. 3.2), cm^2/s: the
