@@ -7,12 +7,15 @@
 //     conditions of Sec. 3.1/3.2), and the tiles of the force region around
 //     the body (penalized nodes and the MEM link terms of Eq. MMEL /
 //     Eq. fluidtorque).  Its SIM and region blocks add their force terms into
-//     exact fixed-point sums and take a ticket; the last of them records the
-//     step's forces and, for a moving body, applies the FP64 rigid-body update
-//     (Eqs. dep1, theta2) and re-rasterises the mask.
+//     exact fixed-point sums.  For a moving body they take a ticket and the
+//     last of them records the step's forces, applies the FP64 rigid-body
+//     update (Eqs. dep1, theta2) and re-rasterises the mask; for a fixed body
+//     one extra block of the next step's launch records them.
 //   * the bulk kernel: every other node -- pull streaming (Eq. eqBd) and the
 //     BGK/TRT collision (Eq. TRT) of fluid nodes whose sources all lie inside
-//     the lattice; no mask, no side conditions, no forces.
+//     the lattice; no mask, no side conditions, no forces.  It comes in
+//     several launch forms with identical results (bulk_kernel for FP32/FP64,
+//     bulk16_kernel and bulk16x4_kernel for 16-bit storage).
 // For the first step after a pre-collision state the special kernel updates
 // every tile.
 #include "vplbm_internal.cuh"

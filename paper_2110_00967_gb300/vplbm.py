@@ -483,9 +483,10 @@ def body_of(w) -> vplbm_body:
 # several lattices stepped together
 # ---------------------------------------------------------------------------
 class Batch:
-    """Lattices stepped in lockstep on one stream (vplbm_batch_*).  Keeps the
-    Lattice objects alive; close() (or garbage collection) releases the batch
-    before them."""
+    """Lattices stepped together (vplbm_batch_*): each lattice's steps run on a
+    stream of their own, forked from and joined to the batch's stream, 32-step
+    runs replayed from one CUDA graph.  Keeps the Lattice objects alive;
+    close() (or garbage collection) releases the batch before them."""
 
     def __init__(self, lattices, stream=None):
         import torch
