@@ -724,10 +724,9 @@ __global__ void __launch_bounds__(kThreads * kTiles) bulk_kernel(const StepArgs 
 }
 
 // ---------------------------------------------------------------------------
-// two nodes at once: the bulk kernel updates each thread's two nodes (rows r
-// and r + 1 of a tile) together.  FP32 uses the packed f32x2 instructions of
-// sm_100 and later (one instruction for both nodes); FP64 has no packed form
-// and runs the two nodes as separate scalar operations.
+// two nodes at once: the 16-bit bulk kernels collide their nodes in pairs
+// with the packed f32x2 instructions of sm_100 and later (one instruction
+// for both nodes of a pair).
 // ---------------------------------------------------------------------------
 struct F2 {
   float2 v;
@@ -755,32 +754,6 @@ __device__ __forceinline__ F2 vsub(F2 a, F2 b) {
 __device__ __forceinline__ F2 vrcp(F2 a) { return vpair(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
 __device__ __forceinline__ float vlo(F2 a) { return a.v.x; }
 __device__ __forceinline__ float vhi(F2 a) { return a.v.y; }
-
-struct D2 {
-  double x, y;
-};
-__device__ __forceinline__ D2 vpair(double x, double y) { return D2{x, y}; }
-__device__ __forceinline__ D2 vsplat(double c) { return D2{c, c}; }
-__device__ __forceinline__ D2 vadd(D2 a, D2 b) { return D2{__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)}; }
-__device__ __forceinline__ D2 vsub(D2 a, D2 b) { return D2{__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)}; }
-__device__ __forceinline__ D2 vmul(D2 a, D2 b) { return D2{__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)}; }
-__device__ __forceinline__ D2 vfma(D2 a, D2 b, D2 c) {
-  return D2{__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y)};
-}
-__device__ __forceinline__ D2 vrcp(D2 a) { return D2{1.0 / a.x, 1.0 / a.y}; }
-__device__ __forceinline__ double vlo(D2 a) { return a.x; }
-__device__ __forceinline__ double vhi(D2 a) { return a.y; }
-
-template <typename T>
-struct VecOf;
-template <>
-struct VecOf<float> {
-  using type = F2;
-};
-template <>
-struct VecOf<double> {
-  using type = D2;
-};
 
 // The collision of collide() for two nodes, with the relaxation rates and
 // weights folded into the coefficients: for each pair (a, opp(a))
