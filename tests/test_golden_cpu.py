@@ -1,0 +1,56 @@
+"""The stored oracle values under tests/golden/ against what the mathematics
+fixes, so that a corrupted or hand-edited file fails here before any GPU test
+compares with it: the lift of the symmetric airfoil at zero incidence
+vanishes, drag is positive and grows with incidence over the steady angles,
+lift grows with incidence there, the window means are the means of their
+blocks, and the storage envelopes grow as the formats lose precision."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def load(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not written yet")
+    return json.load(open(path))
+
+
+def test_long_means_obey_symmetry_and_monotonicity():
+    d = load("naca512_means.json")
+    ang = d["angles"]
+    for est in ("mem", "sim"):
+        assert abs(ang["0"][f"cl_{est}"]) <= 1e-10  # mirror-symmetric body and lattice
+        cds = [ang[a][f"cd_{est}"] for a in ("0", "5", "10", "15")]
+        cls = [ang[a][f"cl_{est}"] for a in ("0", "5", "10", "15")]
+        assert all(c > 0 for c in cds) and np.all(np.diff(cds) > 0)
+        assert np.all(np.diff(cls) > 0)
+    for a, r in ang.items():
+        for k in ("cd_mem", "cl_mem", "cd_sim", "cl_sim"):
+            assert len(r[f"{k}_blocks"]) * d["block"] == d["window"][1] - d["window"][0] + 1
+            assert abs(np.mean(r[f"{k}_blocks"]) - r[k]) <= 1e-12 * max(1.0, abs(r[k]))
+
+
+def test_storage_envelopes_grow_with_the_rounding_unit():
+    d = load("storage_envelopes.json")
+    for case in ("naca0-512", "naca10-512"):
+        for offs in ("free-stream", "weights"):
+            f32, f16, bf16 = (d["cases"][f"{case}/{offs}/{f}"] for f in ("f32", "f16", "bf16"))
+            # velocity errors scale with the unit of the format: 2^-24, 2^-11, 2^-8
+            assert max(f32["fields"][1:]) < max(f16["fields"][1:]) < max(bf16["fields"][1:])
+            assert max(f32["fields"][1:]) < 1e-5
+
+
+def test_serving_subset_is_the_seeded_mix():
+    from paper_2110_00967_gb300 import workloads as W
+    d = load("serving_subset.json")
+    reqs = W.serving_requests(256)[:len(d["requests"])]
+    for r, g in zip(reqs, d["requests"]):
+        assert (r.rid, r.nx, r.ny) == (g["rid"], g["nx"], g["ny"])
+        assert r.alpha_deg == g["alpha_deg"]
+        assert g["cd_mem"] > 0 and g["cd_sim"] > 0
+        assert g["cl_mem"] * g["alpha_deg"] >= 0  # lift follows the incidence
