@@ -40,6 +40,9 @@ NX, NY = 2048, 1024
 # 9 x 2 B + 9 x 2 B for the 16-bit offset forms
 BYTES_PER_LUP = {"f32": 72, "f16": 36, "bf16": 36}
 STORAGE_NAME = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}
+# the arithmetic of the step: FP32, with the 16-bit forms storing FP16 / BF16
+# offsets and colliding in FP32 (force sums FP64 in every form)
+DTYPE_NAME = {"f32": "f32", "f16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute"}
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_naca2048_f32.md")
 KERNEL_SOURCES = ("paper_2110_00967_gb300/csrc/step.cu",
                   "paper_2110_00967_gb300/csrc/vplbm_internal.cuh",
@@ -265,30 +268,33 @@ def run_ours(args, rank, world, local_rank):
     for lat in lats:
         lat.check()
 
-    # end-to-end through the public API with host buffers: place the bodies
-    # (geometry and body state up), step, and read every step's forces back
-    # (MEM and SIM, 32 steps at a time) into pinned host memory
-    e2e_steps = max(2 * CHUNK, min(args.steps, 2000) // CHUNK * CHUNK)
-    pinned = torch.empty((len(lats), e2e_steps // CHUNK, 2, CHUNK, 3), dtype=torch.float64,
-                         pin_memory=True).numpy()
+    # end-to-end through the public API with host buffers, as a solve runs:
+    # place the bodies (geometry and body state up), step, and read every
+    # step's forces back (MEM, SIM and the volume integral, 32 steps at a
+    # time, queued into pinned host memory behind each run of steps); one
+    # synchronisation at the end.  At least 1024 steps, so that placing the
+    # bodies weighs as it does in a solve of many steps.
+    e2e_steps = max(1024, -(-args.steps // CHUNK) * CHUNK)
+    n_chunks = e2e_steps // CHUNK
+    pinned = torch.empty((len(lats), n_chunks, CHUNK, 9), dtype=torch.float64, pin_memory=True)
+    rows = pinned.numpy()
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     for w, lat in zip(works, lats):
         lat.set_body(V.body_of(w))
-    for c in range(e2e_steps // CHUNK):
+    for c in range(n_chunks):
         batch.step(CHUNK)
         for i, lat in enumerate(lats):
-            pinned[i, c, 0] = lat.history(V.MEM, CHUNK)
-            pinned[i, c, 1] = lat.history(V.SIM, CHUNK)
+            V.vplbm_force_history_async(lat.ctx, CHUNK, rows[i, c].ctypes.data)
     torch.cuda.synchronize()
     e2e_dt = reduce_max(time.perf_counter() - t0, world, dev)
-    assert np.isfinite(pinned).all()
+    assert np.isfinite(rows[:, :, :, :3]).all() and np.isfinite(rows[:, :, :, 3:6]).all()
     # host -> device per lattice and set_body: the body state and the force region (two
-    # buffers each, 152 and 24 bytes) and the 849 SIM points (64 bytes each)
-    h2d = len(lats) * (2 * 152 + 2 * 24 + 849 * 64) / e2e_steps
-    # device -> host per lattice and step: one history row (6 doubles) per estimator read
-    d2h = len(lats) * 2 * 6 * 8
+    # buffers each, 152 and 24 bytes) and the 849 SIM points (72 bytes each)
+    h2d = len(lats) * (2 * 152 + 2 * 24 + 849 * 72) / e2e_steps
+    # device -> host per lattice and step: one history row (9 doubles)
+    d2h = len(lats) * 9 * 8
     batch.close()
 
     nodes = NX * NY * len(lats)
@@ -304,7 +310,8 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed_ms / args.steps, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.dtype],
+        "data": "synthetic",
         "config": config_block(args.dtype, {"parallelism": f"replicas{world}",
                                             "bulk_variant": variants}),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -328,7 +335,7 @@ def run_ours(args, rank, world, local_rank):
 def run_sedimentation(args, rank, world, local_rank, paper=False):
     """The sedimentation box (400 x 1600 FP32, disk D = 50, rho_s/rho = 1.03,
     rigid body driven by MEM in one run and by SIM in the other), or with
-    `paper` the paper's own channel (3120 x 208, D = 26, zero-velocity inlet
+    `paper` the paper's own channel (1560 x 104, D = 26, zero-velocity inlet
     above, free outlet below; the four density ratios, each driven by MEM and
     by SIM: eight lattices), released at rest and stepped warmup + steps
     times; the timed region covers the last `steps` steps of every run.
@@ -418,7 +425,8 @@ def run_sedimentation(args, rank, world, local_rank, paper=False):
 def run_serving(args, rank, world, local_rank):
     """A seeded mix of NACA 0012 solves served to convergence (continuous
     batching under a memory budget); Poisson arrivals at 4 / (estimated mean
-    solve time of one request alone)."""
+    solve time of one request alone).  `value` counts converged solves only;
+    requests stopped at the step cap are reported apart."""
     import torch
     from paper_2110_00967_gb300 import serve as S
     from paper_2110_00967_gb300 import vplbm as V
@@ -456,7 +464,7 @@ def run_serving(args, rank, world, local_rank):
     return {
         "metric": "solves/s", "value": round(world * summ["solves_per_s"], 4), "unit": "solves/s",
         "n_gpus": world, "steps": args.cap, "warmup": 1, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.dtype], "data": "synthetic",
         "config": {"workload": f"naca0012-serving-{args.requests}req-seed2110-{args.dtype}",
                    "grids": [list(g) for g in W.SERVING_GRIDS], "alpha_deg": [0, 20],
                    "arrival_rate_per_s": round(rate, 4), "window": 1000, "tol": 1e-4,
@@ -464,6 +472,9 @@ def run_serving(args, rank, world, local_rank):
                    "max_active": args.max_active or "memory-bound",
                    "parallelism": f"replicas{world}"},
         "p50_s": round(summ["p50_s"], 4), "p99_s": round(summ["p99_s"], 4),
+        "latency": "arrival to converged Cd/Cl, converged requests only",
+        "completed_per_s": round(world * summ["completed_per_s"], 4),
+        "p50_all_s": round(summ["p50_all_s"], 4), "p99_all_s": round(summ["p99_all_s"], 4),
         "converged": summ["converged"], "capped": summ["capped"],
         "rejected": summ["rejected"], "aggregate_mlups": round(world * summ["mlups"], 1),
         "elapsed_s": round(elapsed, 3),
@@ -515,7 +526,7 @@ def run_naca_large(args, rank, world, local_rank):
         "metric": METRIC, "value": round(world * nodes * args.steps / (elapsed_ms / 1e3) / 1e6, 1),
         "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(step_ms, 5), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE_NAME[args.dtype], "data": "synthetic",
         "config": {"workload": f"naca0012-8192x4096-{args.dtype}-alpha10", "grid": [w.nx, w.ny],
                    "instances": 1, "chord": 800, "reynolds": 1000, "tau_plus": 0.62,
                    "storage": args.dtype, "bulk_variant": [variant],
@@ -678,7 +689,7 @@ def run_naca_paper(args, rank, world, local_rank, sim_variants=False):
         "metric": METRIC, "value": round(world * nodes * args.steps / (elapsed_ms / 1e3) / 1e6, 1),
         "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed_ms / args.steps, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.dtype], "data": "synthetic",
         "config": {"workload": (f"naca0012-paper-3614x1946-{args.dtype}-alpha12-sim-variants"
                                 if sim_variants else
                                 f"naca0012-paper-3614x1946-{args.dtype}-alpha0..28-10angles"),
@@ -737,8 +748,8 @@ def main(argv=None):
                          "ratios, MEM and SIM (20,280 steps per physical second); sim-variants: "
                          "the paper's NACA case at 12 degrees once per SIM point count and "
                          "order; naca-large: one 8192 x 4096 lattice")
-    ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
-    ap.add_argument("--cap", type=int, default=20000, help="serving: step cap per request")
+    ap.add_argument("--requests", type=int, default=256, help="serving: number of requests")
+    ap.add_argument("--cap", type=int, default=200000, help="serving: step cap per request")
     ap.add_argument("--memory-gb", type=int, default=40, help="serving: device-memory budget")
     ap.add_argument("--max-active", type=int, default=0,
                     help="serving: most requests stepped at once (0: as many as fit; 1: one "

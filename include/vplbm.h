@@ -195,6 +195,15 @@ vplbm_status vplbm_forces_async(vplbm_ctx *ctx, double *out);
  * or the number of steps taken. */
 vplbm_status vplbm_force_history(vplbm_ctx *ctx, int32_t estimator, int32_t count, double *out);
 
+/* The last `count` history rows, queued into caller host memory without
+ * waiting: out[count][9] = MEM (F_x, F_y, T), SIM (F_x, F_y, T; NaN on steps
+ * without SIM), volume integral (F_x, F_y, T), oldest first.  out should be
+ * page-locked for the copy to be asynchronous; it is valid once the stream
+ * has been synchronised, and a later vplbm_step that wraps the ring past
+ * these rows must be queued after the copy (the same stream orders it).
+ * EINVAL when count exceeds the history length or the steps taken. */
+vplbm_status vplbm_force_history_async(vplbm_ctx *ctx, int32_t count, double *out);
+
 /* FP64 sums of (F_x, F_y, T) of both estimators since the last reset and the
  * number of steps summed (host outputs sums[6] = MEM then SIM, n[2]). */
 vplbm_status vplbm_force_sums(vplbm_ctx *ctx, double sums[6], int64_t n[2]);
@@ -203,14 +212,25 @@ vplbm_status vplbm_reset_sums(vplbm_ctx *ctx);
 /* Number of steps taken since vplbm_set_body (host output). */
 vplbm_status vplbm_step_count(vplbm_ctx *ctx, int64_t *n);
 
-/* Pre-collision populations f_a of the current time level as FP64 into the
- * caller's device buffer f_dev[9][ny][nx] (the streamed field: Eq. eqBd's
- * left-hand side).  Queued on the stream. */
-vplbm_status vplbm_get_f(vplbm_ctx *ctx, double *f_dev);
+/* Pre-collision populations f_a of the current time level (the streamed
+ * field: Eq. eqBd's left-hand side) as FP64 into caller host memory
+ * f[9][ny][nx].  Synchronises the stream.  The rows are staged a few at a
+ * time in the population buffer that does not hold the state, so the call
+ * needs no device memory beyond the workspace.  ESTATE before
+ * vplbm_set_body. */
+vplbm_status vplbm_get_f(vplbm_ctx *ctx, double *f);
 
 /* Macroscopic fields of the current time level (Eqs. updatestep,
- * updatestepm) as FP64 into caller device buffers [ny][nx] each.  Queued. */
-vplbm_status vplbm_get_fields(vplbm_ctx *ctx, double *rho_dev, double *ux_dev, double *uy_dev);
+ * updatestepm: rho, and the penalized velocity u on solid nodes) as FP64 into
+ * caller host memory rho[ny][nx], ux[ny][nx], uy[ny][nx].  Synchronises the
+ * stream; staged as vplbm_get_f.  ESTATE before vplbm_set_body. */
+vplbm_status vplbm_get_fields(vplbm_ctx *ctx, double *rho, double *ux, double *uy);
+
+/* The same two read-backs into caller device memory (f_dev[9][ny][nx];
+ * rho_dev, ux_dev, uy_dev [ny][nx] each), queued on the stream without
+ * waiting. */
+vplbm_status vplbm_get_f_dev(vplbm_ctx *ctx, double *f_dev);
+vplbm_status vplbm_get_fields_dev(vplbm_ctx *ctx, double *rho_dev, double *ux_dev, double *uy_dev);
 
 /* Overwrites the state from caller device FP64 buffers [9][ny][nx].
  * post_collision = 0: f_dev is the pre-collision field of the current time
@@ -222,9 +242,39 @@ vplbm_status vplbm_get_fields(vplbm_ctx *ctx, double *rho_dev, double *ux_dev, d
 vplbm_status vplbm_set_state(vplbm_ctx *ctx, const double *f_dev, const double *prev_dev,
                              int32_t post_collision);
 
-/* Mask chi of the current time level (0 fluid, 1 solid) into caller device
- * memory [ny][nx] bytes.  Queued. */
-vplbm_status vplbm_get_mask(vplbm_ctx *ctx, uint8_t *chi_dev);
+/* Mask chi of the current time level (Eq. fcar: 1 on nodes inside or on
+ * the body, 0 elsewhere) into caller host memory chi[ny][nx] bytes.
+ * Synchronises the stream; staged as vplbm_get_f. */
+vplbm_status vplbm_get_mask(vplbm_ctx *ctx, uint8_t *chi);
+
+/* The mask into caller device memory chi_dev[ny][nx], queued. */
+vplbm_status vplbm_get_mask_dev(vplbm_ctx *ctx, uint8_t *chi_dev);
+
+/* ---- checkpoint and restart ----
+ * No counterpart in the paper (its runs are single uninterrupted solves).
+ * A snapshot holds everything a lattice continues from: the stored
+ * populations of the current time level, the outlet columns, the mask, the
+ * SIM polygon and its sampled nodes, the force histories, running sums and
+ * counts, the step counter, the body and force-region states (FP64) and the
+ * library's host-side bookkeeping, as raw bytes.  A lattice restored from it
+ * continues bit for bit as the saved one would have: the same populations,
+ * forces, body trajectory and sums, in every storage form, fixed or moving
+ * body.
+ *
+ * vplbm_state_bytes: the snapshot size of this lattice (host output).
+ * vplbm_save_state: writes the snapshot into caller host memory of at least
+ *   that many bytes (the pending force sums are finalized first, so the
+ *   history is complete); synchronises the stream.  ESTATE before
+ *   vplbm_set_body; EINVAL when bytes is too small.
+ * vplbm_load_state: restores a snapshot into this lattice, which may be the
+ *   one it was taken from or another created with an identical
+ *   configuration (any workspace address); the body placed by the snapshot
+ *   replaces the current one.  Synchronises the stream.  EINVAL for a buffer
+ *   that is not a snapshot of this library's format, or of a lattice with
+ *   another configuration.  Step graphs are rebuilt at the next step. */
+vplbm_status vplbm_state_bytes(vplbm_ctx *ctx, size_t *bytes);
+vplbm_status vplbm_save_state(vplbm_ctx *ctx, void *host, size_t bytes);
+vplbm_status vplbm_load_state(vplbm_ctx *ctx, const void *host, size_t bytes);
 
 /* Body state (x_c, y_c, angle, u_x, u_y, omega), host output.  Synchronises. */
 vplbm_status vplbm_get_body(vplbm_ctx *ctx, double state[6]);
@@ -317,21 +367,24 @@ void vplbm_batch_destroy(vplbm_batch *batch);
  * exact tie, walk along the lattice direction closest to the normal to the
  * first fluid node, stress averaged over the candidates, summed in point
  * order in FP64) on the inputs given here.
- *   cfg     nx, ny, tau_plus and body_force are used;
+ *   cfg     nx, ny, tau_plus and body_force are used; sim_order must be 0 (the
+ *           stress copied from the sampled node, as Sec. 2.3.2 describes;
+ *           EINVAL otherwise);
  *   f_dev   device, FP64 pre-collision populations [9][ny][nx];
  *   chi_dev device, mask [ny][nx] (0 fluid, nonzero solid);
  *   pts     host, n_pts rows (x - ref_x, y - ref_y, n_x, n_y, S);
  *   ref     host, the reference point; out host, (F_x, F_y, T).
  * The scratch is one fixed device array in the library of
  * 8 * (8 + 4096) doubles (256 KiB), held by every GPU that loads the library
- * until the process exits: n_pts above 4096 is rejected with EINVAL.  The
- * first call on a device takes that array's device address with the device
- * current; make that first call before any stream capture.  Every call uses
- * the same array and leaves its contents behind (the call clears what must
- * start at zero), so calls whose GPU work overlaps -- on two streams or from
- * two threads -- race.  Synchronises cuda_stream; ESTATE when a point finds
- * no fluid node (out then sums the other points); the text of a failure is
- * vplbm_last_error(NULL). */
+ * until the process exits: n_pts above 4096 is rejected with EINVAL.  Every
+ * call takes that array's device address with the device current
+ * (cudaGetSymbolAddress, which allocates nothing); the first call on a device
+ * also loads the library's device code there, so make it before any stream
+ * capture.  Every call uses the same array and leaves its contents behind
+ * (the call clears what must start at zero), so calls whose GPU work
+ * overlaps -- on two streams or from two threads -- race.  Synchronises
+ * cuda_stream; ESTATE when a point finds no fluid node (out then sums the
+ * other points); the text of a failure is vplbm_last_error(NULL). */
 vplbm_status vplbm_sim_force_static(const vplbm_config *cfg, const double *f_dev,
                                     const uint8_t *chi_dev, int32_t n_pts, const double *pts,
                                     const double ref[2], double out[3], void *cuda_stream);

@@ -9,14 +9,29 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "vplbm_internal.cuh"
 
 using namespace vplbm;
 
 namespace {
 
+// An NVTX range around a call, for timelines taken with a profiler (the
+// calls cost nothing measurable when no profiler is attached).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
+
 constexpr size_t kAlign = 256;
-constexpr int kGraphPairs = 16;  // a captured graph holds 2 * kGraphPairs steps
+// Runs of steps are replayed from CUDA graphs of 1, 2, 4, ..., 32 steps, one
+// per length and per starting buffer: any step count is a sum of at most
+// kGraphLevels graph launches per 63 steps.
+constexpr int kGraphLevels = 6;
+constexpr int kGraphMax = 1 << (kGraphLevels - 1);  // 32 steps
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -223,6 +238,7 @@ struct vplbm_ctx {
   bool pre = true;    // the state is a pre-collision field (first step reads in place)
   bool pending = false;      // the last queued step's force sums still await finalizing
   bool pending_sim = false;  // ... and that step evaluated SIM
+  bool mask_stale = false;   // a moving body's chi lags its body by a step
   bool has_body = false;
   vplbm_body body_cfg{};
   BodyState body_host{};
@@ -232,7 +248,9 @@ struct vplbm_ctx {
   long long steps = 0;
   int64_t launches = 0;
   uint64_t generation = 0;  // bumped whenever captured step graphs go stale
-  cudaGraphExec_t graph = nullptr;  // 2 * kGraphPairs steps starting from buffer 0
+  // graphs[p][k]: 2^k steps starting from buffer p, ending with finalized forces
+  cudaGraphExec_t graphs[2][kGraphLevels] = {};
+  bool graphs_ready = false;
   cudaStream_t side = nullptr;      // the special kernel's stream
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int region_slots = 1;             // blocks reserved for force-region tiles
@@ -315,6 +333,7 @@ StepArgs step_args(vplbm_ctx *c, int src, bool do_sim) {
   a.edge_blocks = (a.n_edge + kThreads - 1) / kThreads;
   a.region_slots = c->region_slots;
   a.region_capacity = kRegionCapacity;
+  a.raster = c->body_host.moving ? 1 : 0;
   return a;
 }
 
@@ -339,7 +358,18 @@ cudaError_t flush_forces(vplbm_ctx *c, cudaStream_t s) {
   return launch_finalize(c->cfg.dtype, a, s);
 }
 
+// A moving body's steps leave chi one time level behind the body (each step
+// rasterises the level it updates): one launch brings it to the current
+// level, at the end of every call and every step graph.
+cudaError_t refresh_mask(vplbm_ctx *c, cudaStream_t s) {
+  if (!c->mask_stale) return cudaSuccess;
+  c->mask_stale = false;
+  ++c->launches;
+  return launch_mask(step_args(c, c->cur, false), s);
+}
+
 cudaError_t queue_step(vplbm_ctx *c, cudaStream_t s, int src, bool pre, bool do_sim) {
+  if (c->body_host.moving) c->mask_stale = true;
   if (pre) {
     cudaError_t e = flush_forces(c, s);
     StepArgs a = step_args(c, src, do_sim);
@@ -376,32 +406,74 @@ vplbm_status one_step(vplbm_ctx *c, cudaStream_t s) {
   return VPLBM_OK;
 }
 
-// graph of 2 * kGraphPairs gather steps starting from buffer 0; valid when
-// SIM runs every step or never (the step kernels are then identical)
-vplbm_status ensure_graph(vplbm_ctx *c) {
-  if (c->graph) return VPLBM_OK;
+void drop_graphs(vplbm_ctx *c) {
+  for (auto &row : c->graphs)
+    for (cudaGraphExec_t &g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+  c->graphs_ready = false;
+}
+
+// the longest graph that fits in `left` steps: its level k (2^k steps)
+int graph_level(int left) {
+  int k = 0;
+  while (k + 1 < kGraphLevels && (2 << k) <= left) ++k;
+  return k;
+}
+
+// Captures the step graphs of every length and both starting buffers (valid
+// when SIM runs every step or never: the step kernels are then the same for
+// every step).  Each graph begins with no force sums pending and ends with
+// its last step's sums finalized.  All are captured together, at the first
+// run that needs one, so that later runs of any length find theirs.
+vplbm_status ensure_graphs(vplbm_ctx *c) {
+  if (c->graphs_ready) return VPLBM_OK;
   if (!c->capture_stream)
     VPLBM_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
-  cudaGraph_t g = nullptr;
-  VPLBM_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaSuccess;
   const int64_t launches = c->launches;
-  for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
-    e = queue_step(c, c->capture_stream, k & 1, false, c->sim_every == 1 && c->n_sim > 0);
-  if (e == cudaSuccess) e = flush_forces(c, c->capture_stream);  // the graph ends finalized
-  c->launches = launches;  // counted when the graph is launched
-  cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
-  if (e != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    return cuda_fail(c, e, "capture of the step graph");
-  }
-  if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&c->graph, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    c->graph = nullptr;
-    return cuda_fail(c, e, "cudaGraphInstantiate");
-  }
+  const bool stale = c->mask_stale;
+  const bool do_sim = c->sim_every == 1 && c->n_sim > 0;
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < kGraphLevels; ++k) {
+      cudaGraph_t g = nullptr;
+      VPLBM_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      const int cur = c->cur;
+      c->cur = (p + (1 << k)) & 1;  // the mask refresh reads the level the graph ends at
+      for (int q = 0; q < (1 << k) && e == cudaSuccess; ++q)
+        e = queue_step(c, c->capture_stream, (p + q) & 1, false, do_sim);
+      if (e == cudaSuccess) e = flush_forces(c, c->capture_stream);
+      if (e == cudaSuccess) e = refresh_mask(c, c->capture_stream);
+      c->cur = cur;
+      c->launches = launches;  // counted when a graph is launched
+      c->mask_stale = stale;
+      const cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
+      if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        drop_graphs(c);
+        return cuda_fail(c, e, "capture of a step graph");
+      }
+      if (e2 != cudaSuccess) {
+        drop_graphs(c);
+        return cuda_fail(c, e2, "cudaStreamEndCapture");
+      }
+      e = cudaGraphInstantiate(&c->graphs[p][k], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        c->graphs[p][k] = nullptr;
+        drop_graphs(c);
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+      }
+      // uploaded now, so that the first launch of each does not pay for it
+      e = cudaGraphUpload(c->graphs[p][k], c->stream);
+      if (e != cudaSuccess) {
+        drop_graphs(c);
+        return cuda_fail(c, e, "cudaGraphUpload");
+      }
+    }
+  c->graphs_ready = true;
   return VPLBM_OK;
 }
 
@@ -420,10 +492,7 @@ constexpr int kTuneRounds = 3;
 void set_variant(vplbm_ctx *c, int v) {
   if (v == c->bulk_variant) return;
   c->bulk_variant = v;
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  drop_graphs(c);
   ++c->generation;  // batches re-capture their graphs
 }
 
@@ -575,6 +644,7 @@ vplbm_status vplbm_set_stream(vplbm_ctx *c, void *cuda_stream) {
 }
 
 vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
+  Range range_("vplbm_set_body");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!b) return fail(c, VPLBM_EINVAL, "body is NULL");
   const Lattice &L = c->L;
@@ -676,10 +746,7 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
   c->region_slots = std::max(1, slots);
   c->n_sim = n_sim;
   c->sim_every = (b->moving && b->estimator == VPLBM_SIM) ? 1 : c->cfg.sim_every;
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  drop_graphs(c);
   ++c->generation;
   cudaStream_t s = c->stream;
   c->region_host = reg;
@@ -691,8 +758,17 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
     VPLBM_CUDA(c, cudaMemcpyAsync(c->sim_pts, pts.data(), n_sim * sizeof(SimPoint), cudaMemcpyHostToDevice, s));
   VPLBM_CUDA(c, cudaMemsetAsync(c->chi, 0, (size_t)L.pitch * L.ny, s));
   if (b->kind != VPLBM_BODY_NONE) {
-    VPLBM_CUDA(c, launch_raster(L, c->body[0], c->chi, 0, 0, L.nx - 1, L.ny - 1, s));
-    VPLBM_CUDA(c, launch_interface(L, c->chi, 0, 0, L.nx - 1, L.ny - 1, s));
+    // the predicate only where the body can be: its polygon's box with a
+    // margin of three nodes (the surface bulges beyond the polygon's edges
+    // by far less than a node); interface bits one node wider
+    int i0 = std::max(0, (int)floor(bx0) - 3), i1 = std::min(L.nx - 1, (int)ceil(bx1) + 3);
+    int j0 = std::max(0, (int)floor(by0) - 3), j1 = std::min(L.ny - 1, (int)ceil(by1) + 3);
+    // a box reaching a periodic side: its neighbours across the side too
+    if (L.bc[0] == VPLBM_PERIODIC && (i0 == 0 || i1 == L.nx - 1)) i0 = 0, i1 = L.nx - 1;
+    if (L.bc[2] == VPLBM_PERIODIC && (j0 == 0 || j1 == L.ny - 1)) j0 = 0, j1 = L.ny - 1;
+    VPLBM_CUDA(c, launch_raster(L, c->body[0], c->chi, i0, j0, i1, j1, s));
+    VPLBM_CUDA(c, launch_interface(L, c->chi, std::max(0, i0 - 1), std::max(0, j0 - 1),
+                                   std::min(L.nx - 1, i1 + 1), std::min(L.ny - 1, j1 + 1), s));
     c->launches += 2;
   }
   VPLBM_CUDA(c, launch_init(c->cfg.dtype, L, c->body[0], c->chi, c->buf[0], c->cfg.u_in[0], c->cfg.u_in[1], s));
@@ -707,11 +783,13 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
   c->pre = true;
   c->steps = 0;
   c->pending = false;  // the accumulators were cleared with the other counters
+  c->mask_stale = false;
   c->has_body = true;
   return sync(c);
 }
 
 vplbm_status vplbm_step(vplbm_ctx *c, int32_t nsteps) {
+  Range range_("vplbm_step");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (nsteps < 0) return fail(c, VPLBM_EINVAL, "nsteps must be >= 0");
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "no body placed (vplbm_set_body)");
@@ -719,20 +797,25 @@ vplbm_status vplbm_step(vplbm_ctx *c, int32_t nsteps) {
   int left = nsteps;
   const bool graphable = c->sim_every <= 1;
   while (left > 0) {
-    if (graphable && !c->pre && c->cur == 0 && left >= 2 * kGraphPairs) {
+    if (graphable && !c->pre) {
+      // the longest captured run that fits, from the current buffer
       VPLBM_CUDA(c, flush_forces(c, s));  // a graph starts with nothing pending
-      if (vplbm_status st = ensure_graph(c)) return st;
-      VPLBM_CUDA(c, cudaGraphLaunch(c->graph, s));
-      c->launches += 4 * kGraphPairs + 1;
-      c->steps += 2 * kGraphPairs;
+      if (vplbm_status st = ensure_graphs(c)) return st;
+      const int k = graph_level(left), n = 1 << k;
+      VPLBM_CUDA(c, cudaGraphLaunch(c->graphs[c->cur][k], s));
+      c->launches += 2 * n + 1 + (c->body_host.moving ? 1 : 0);
+      c->steps += n;
+      c->cur ^= n & 1;
       c->pending = false;
-      left -= 2 * kGraphPairs;
+      c->mask_stale = false;  // the graph ends with the mask refreshed
+      left -= n;
       continue;
     }
     if (vplbm_status st = one_step(c, s)) return st;
     --left;
   }
   VPLBM_CUDA(c, flush_forces(c, s));  // every call returns with its forces finalized
+  VPLBM_CUDA(c, refresh_mask(c, s));  // and with the mask of the current level
   return VPLBM_OK;
 }
 
@@ -745,6 +828,7 @@ static vplbm_status read_hist_entry(vplbm_ctx *c, long long step, double out[kHi
 }
 
 vplbm_status vplbm_force_mem(vplbm_ctx *c, double F[2], double *T) {
+  Range range_("vplbm_force_mem");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!F || !T) return fail(c, VPLBM_EINVAL, "NULL output");
   if (c->steps == 0) return fail(c, VPLBM_ESTATE, "no step taken");
@@ -760,6 +844,7 @@ vplbm_status vplbm_force_mem(vplbm_ctx *c, double F[2], double *T) {
 }
 
 vplbm_status vplbm_force_sim(vplbm_ctx *c, double F[2], double *T) {
+  Range range_("vplbm_force_sim");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!F || !T) return fail(c, VPLBM_EINVAL, "NULL output");
   if (c->sim_every <= 0 || c->n_sim <= 0 || c->steps == 0) return fail(c, VPLBM_ESTATE, "SIM not evaluated");
@@ -778,6 +863,7 @@ vplbm_status vplbm_force_sim(vplbm_ctx *c, double F[2], double *T) {
 }
 
 vplbm_status vplbm_force_angot(vplbm_ctx *c, double F[2], double *T) {
+  Range range_("vplbm_force_angot");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!F || !T) return fail(c, VPLBM_EINVAL, "NULL output");
   if (c->steps == 0) return fail(c, VPLBM_ESTATE, "no step taken");
@@ -790,6 +876,7 @@ vplbm_status vplbm_force_angot(vplbm_ctx *c, double F[2], double *T) {
 }
 
 vplbm_status vplbm_forces_async(vplbm_ctx *c, double *out) {
+  Range range_("vplbm_forces_async");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!out) return fail(c, VPLBM_EINVAL, "NULL output");
   if (c->steps == 0) return fail(c, VPLBM_ESTATE, "no step taken");
@@ -800,6 +887,7 @@ vplbm_status vplbm_forces_async(vplbm_ctx *c, double *out) {
 }
 
 vplbm_status vplbm_force_history(vplbm_ctx *c, int32_t estimator, int32_t count, double *out) {
+  Range range_("vplbm_force_history");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   const int len = effective_hist(c->cfg);
   if (!out || count < 0 || count > len || count > c->steps)
@@ -823,7 +911,26 @@ vplbm_status vplbm_force_history(vplbm_ctx *c, int32_t estimator, int32_t count,
   return VPLBM_OK;
 }
 
+vplbm_status vplbm_force_history_async(vplbm_ctx *c, int32_t count, double *out) {
+  Range range_("vplbm_force_history_async");
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  const int len = effective_hist(c->cfg);
+  if (!out || count < 0 || count > len || count > c->steps)
+    return fail(c, VPLBM_EINVAL, "bad history request");
+  if (count == 0) return VPLBM_OK;
+  const int first = (int)((c->steps - count) % len);
+  const int n1 = std::min(count, len - first);
+  const size_t row = kHistCols * sizeof(double);
+  VPLBM_CUDA(c, cudaMemcpyAsync(out, c->hist + kHistCols * (size_t)first, (size_t)n1 * row,
+                                cudaMemcpyDeviceToHost, c->stream));
+  if (count > n1)
+    VPLBM_CUDA(c, cudaMemcpyAsync(out + kHistCols * (size_t)n1, c->hist, (size_t)(count - n1) * row,
+                                  cudaMemcpyDeviceToHost, c->stream));
+  return VPLBM_OK;
+}
+
 vplbm_status vplbm_force_sums(vplbm_ctx *c, double sums[6], int64_t n[2]) {
+  Range range_("vplbm_force_sums");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!sums || !n) return fail(c, VPLBM_EINVAL, "NULL output");
   long long cnt[2];
@@ -848,27 +955,131 @@ vplbm_status vplbm_step_count(vplbm_ctx *c, int64_t *n) {
   return VPLBM_OK;
 }
 
-vplbm_status vplbm_get_f(vplbm_ctx *c, double *f_dev) {
+vplbm_status vplbm_get_f_dev(vplbm_ctx *c, double *f_dev) {
+  Range range_("vplbm_get_f_dev");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!f_dev) return fail(c, VPLBM_EINVAL, "f_dev is NULL");
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "no state yet");
-  VPLBM_CUDA(c, launch_get_f(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], f_dev, c->stream));
+  VPLBM_CUDA(c, launch_get_f(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], f_dev, 0,
+                             9, 0, c->L.ny, c->stream));
   ++c->launches;
   return VPLBM_OK;
 }
 
-vplbm_status vplbm_get_fields(vplbm_ctx *c, double *rho, double *ux, double *uy) {
+vplbm_status vplbm_get_fields_dev(vplbm_ctx *c, double *rho, double *ux, double *uy) {
+  Range range_("vplbm_get_fields_dev");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!rho || !ux || !uy) return fail(c, VPLBM_EINVAL, "NULL output");
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "no state yet");
   VPLBM_CUDA(c, launch_get_fields(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], c->chi,
-                                  c->body[c->cur], c->half_pen, rho, ux, uy, c->stream));
+                                  c->body[c->cur], c->half_pen, rho, ux, uy, 0, c->L.ny, c->stream));
   ++c->launches;
   return VPLBM_OK;
 }
 
+vplbm_status vplbm_get_mask_dev(vplbm_ctx *c, uint8_t *chi_dev) {
+  Range range_("vplbm_get_mask_dev");
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!chi_dev) return fail(c, VPLBM_EINVAL, "chi_dev is NULL");
+  VPLBM_CUDA(c, launch_get_mask(c->L, c->chi, chi_dev, 0, c->L.ny, c->stream));
+  ++c->launches;
+  return VPLBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The host read-backs stage their rows in the population buffer that does
+// not hold the state (the next step overwrites it anyway), a few rows at a
+// time, so that they need no device memory beyond the workspace.
+void *staging(const vplbm_ctx *c, size_t *bytes) {
+  *bytes = 9 * (size_t)c->L.plane * elem_bytes(c->cfg.dtype);
+  return c->buf[1 - c->cur];
+}
+
+int rows_per_chunk(size_t staging_bytes, size_t row_bytes, int ny) {
+  const size_t r = staging_bytes / row_bytes;
+  return (int)std::min<size_t>(r, (size_t)ny);
+}
+
+}  // namespace
+
+extern "C" {
+
+vplbm_status vplbm_get_f(vplbm_ctx *c, double *f) {
+  Range range_("vplbm_get_f");
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!f) return fail(c, VPLBM_EINVAL, "NULL output");
+  if (!c->has_body) return fail(c, VPLBM_ESTATE, "no state yet");
+  size_t sb = 0;
+  double *st = static_cast<double *>(staging(c, &sb));
+  const int nx = c->L.nx, ny = c->L.ny;
+  const size_t n = (size_t)nx * ny;
+  // all nine planes of a chunk of rows at once, or (16-bit storage on very
+  // short lattices) one plane at a time
+  const int na = rows_per_chunk(sb, 9 * (size_t)nx * sizeof(double), ny) >= 1 ? 9 : 1;
+  const int rows = rows_per_chunk(sb, (size_t)na * nx * sizeof(double), ny);
+  if (rows < 1) return fail(c, VPLBM_EINVAL, "lattice row too long to stage");
+  for (int a0 = 0; a0 < 9; a0 += na)
+    for (int j0 = 0; j0 < ny; j0 += rows) {
+      const int r = std::min(rows, ny - j0);
+      VPLBM_CUDA(c, launch_get_f(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], st, a0,
+                                 na, j0, r, c->stream));
+      ++c->launches;
+      const size_t w = (size_t)r * nx * sizeof(double);
+      VPLBM_CUDA(c, cudaMemcpy2DAsync(f + a0 * n + (size_t)j0 * nx, n * sizeof(double), st, w, w, na,
+                                      cudaMemcpyDeviceToHost, c->stream));
+    }
+  return sync(c);
+}
+
+vplbm_status vplbm_get_fields(vplbm_ctx *c, double *rho, double *ux, double *uy) {
+  Range range_("vplbm_get_fields");
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!rho || !ux || !uy) return fail(c, VPLBM_EINVAL, "NULL output");
+  if (!c->has_body) return fail(c, VPLBM_ESTATE, "no state yet");
+  size_t sb = 0;
+  double *st = static_cast<double *>(staging(c, &sb));
+  const int nx = c->L.nx, ny = c->L.ny;
+  const int rows = rows_per_chunk(sb, 3 * (size_t)nx * sizeof(double), ny);
+  if (rows < 1) return fail(c, VPLBM_EINVAL, "lattice row too long to stage");
+  double *out[3] = {rho, ux, uy};
+  for (int j0 = 0; j0 < ny; j0 += rows) {
+    const int r = std::min(rows, ny - j0);
+    const size_t m = (size_t)r * nx;
+    VPLBM_CUDA(c, launch_get_fields(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], c->chi,
+                                    c->body[c->cur], c->half_pen, st, st + m, st + 2 * m, j0, r,
+                                    c->stream));
+    ++c->launches;
+    for (int q = 0; q < 3; ++q)
+      VPLBM_CUDA(c, cudaMemcpyAsync(out[q] + (size_t)j0 * nx, st + q * m, m * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream));
+  }
+  return sync(c);
+}
+
+vplbm_status vplbm_get_mask(vplbm_ctx *c, uint8_t *chi) {
+  Range range_("vplbm_get_mask");
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!chi) return fail(c, VPLBM_EINVAL, "NULL output");
+  size_t sb = 0;
+  uint8_t *st = static_cast<uint8_t *>(staging(c, &sb));
+  const int nx = c->L.nx, ny = c->L.ny;
+  const int rows = rows_per_chunk(sb, (size_t)nx, ny);
+  for (int j0 = 0; j0 < ny; j0 += rows) {
+    const int r = std::min(rows, ny - j0);
+    VPLBM_CUDA(c, launch_get_mask(c->L, c->chi, st, j0, r, c->stream));
+    ++c->launches;
+    VPLBM_CUDA(c, cudaMemcpyAsync(chi + (size_t)j0 * nx, st, (size_t)r * nx, cudaMemcpyDeviceToHost,
+                                  c->stream));
+  }
+  return sync(c);
+}
+
 vplbm_status vplbm_set_state(vplbm_ctx *c, const double *f_dev, const double *prev_dev,
                              int32_t post_collision) {
+  Range range_("vplbm_set_state");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!f_dev) return fail(c, VPLBM_EINVAL, "f_dev is NULL");
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "place a body first");
@@ -884,11 +1095,125 @@ vplbm_status vplbm_set_state(vplbm_ctx *c, const double *f_dev, const double *pr
   return VPLBM_OK;
 }
 
-vplbm_status vplbm_get_mask(vplbm_ctx *c, uint8_t *chi_dev) {
+}  // extern "C"
+
+namespace {
+
+// A snapshot: this header, then the workspace from the outlet columns to its
+// end (outlet columns, mask, SIM points and nodes, force history, body and
+// force-region states, running sums, counters, fixed-point accumulators),
+// then the population buffer that holds the state.  Raw bytes: a restored
+// lattice continues bit for bit as the saved one would have.
+struct SnapHeader {
+  char magic[8];
+  int32_t version, header_bytes;
+  vplbm_config cfg;
+  vplbm_body body_cfg;
+  BodyState body_host;
+  ForceRegion region_host;
+  double sim_const[3];
+  int64_t steps;
+  int32_t cur, pre, n_sim, sim_every, region_slots, pad;
+  uint64_t tail_bytes, pop_bytes;
+};
+constexpr char kSnapMagic[8] = {'V', 'P', 'L', 'B', 'M', 'S', 'N', 'P'};
+constexpr int32_t kSnapVersion = 1;
+
+size_t snap_header_bytes() { return align_up(sizeof(SnapHeader), 64); }
+size_t snap_tail_bytes(const vplbm_ctx *c) { return c->lay.total - c->lay.prev[0]; }
+size_t snap_pop_bytes(const vplbm_ctx *c) { return 9 * (size_t)c->L.plane * elem_bytes(c->cfg.dtype); }
+
+bool same_config(const vplbm_config &a, const vplbm_config &b) {
+  bool eq = a.nx == b.nx && a.ny == b.ny && a.dtype == b.dtype && a.collision == b.collision &&
+            a.forcing == b.forcing && a.sim_every == b.sim_every &&
+            effective_max_sim(a) == effective_max_sim(b) && effective_hist(a) == effective_hist(b) &&
+            a.sim_order == b.sim_order && a.tau_plus == b.tau_plus && a.lambda_trt == b.lambda_trt &&
+            a.eta == b.eta;
+  for (int k = 0; k < 4; ++k) eq = eq && a.bc[k] == b.bc[k];
+  for (int k = 0; k < 2; ++k)
+    eq = eq && a.u_in[k] == b.u_in[k] && a.body_force[k] == b.body_force[k] && a.u_ref[k] == b.u_ref[k];
+  return eq;
+}
+
+}  // namespace
+
+extern "C" {
+
+vplbm_status vplbm_state_bytes(vplbm_ctx *c, size_t *bytes) {
+  if (!c || !bytes) return fail(c, VPLBM_EINVAL, "NULL argument");
+  *bytes = snap_header_bytes() + snap_tail_bytes(c) + snap_pop_bytes(c);
+  return VPLBM_OK;
+}
+
+vplbm_status vplbm_save_state(vplbm_ctx *c, void *host, size_t bytes) {
+  Range range_("vplbm_save_state");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
-  if (!chi_dev) return fail(c, VPLBM_EINVAL, "chi_dev is NULL");
-  VPLBM_CUDA(c, launch_get_mask(c->L, c->chi, chi_dev, c->stream));
-  ++c->launches;
+  if (!host) return fail(c, VPLBM_EINVAL, "NULL output");
+  if (!c->has_body) return fail(c, VPLBM_ESTATE, "no state yet");
+  const size_t hb = snap_header_bytes(), tb = snap_tail_bytes(c), pb = snap_pop_bytes(c);
+  if (bytes < hb + tb + pb) return fail(c, VPLBM_EINVAL, fmt("snapshot needs %zu bytes", hb + tb + pb));
+  VPLBM_CUDA(c, flush_forces(c, c->stream));  // the last step's sums into the history first
+  VPLBM_CUDA(c, refresh_mask(c, c->stream));
+  SnapHeader h{};
+  memcpy(h.magic, kSnapMagic, sizeof h.magic);
+  h.version = kSnapVersion;
+  h.header_bytes = (int32_t)hb;
+  h.cfg = c->cfg;
+  h.body_cfg = c->body_cfg;
+  h.body_host = c->body_host;
+  h.region_host = c->region_host;
+  for (int k = 0; k < 3; ++k) h.sim_const[k] = c->sim_const[k];
+  h.steps = c->steps;
+  h.cur = c->cur;
+  h.pre = c->pre ? 1 : 0;
+  h.n_sim = c->n_sim;
+  h.sim_every = c->sim_every;
+  h.region_slots = c->region_slots;
+  h.tail_bytes = tb;
+  h.pop_bytes = pb;
+  char *out = static_cast<char *>(host);
+  memset(out, 0, hb);
+  memcpy(out, &h, sizeof h);
+  VPLBM_CUDA(c, cudaMemcpyAsync(out + hb, c->ws + c->lay.prev[0], tb, cudaMemcpyDeviceToHost, c->stream));
+  VPLBM_CUDA(c, cudaMemcpyAsync(out + hb + tb, c->buf[c->cur], pb, cudaMemcpyDeviceToHost, c->stream));
+  return sync(c);
+}
+
+vplbm_status vplbm_load_state(vplbm_ctx *c, const void *host, size_t bytes) {
+  Range range_("vplbm_load_state");
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (!host) return fail(c, VPLBM_EINVAL, "NULL input");
+  const size_t hb = snap_header_bytes(), tb = snap_tail_bytes(c), pb = snap_pop_bytes(c);
+  if (bytes < hb + tb + pb) return fail(c, VPLBM_EINVAL, "snapshot too short for this lattice");
+  SnapHeader h;
+  memcpy(&h, host, sizeof h);
+  if (memcmp(h.magic, kSnapMagic, sizeof h.magic) != 0 || h.version != kSnapVersion ||
+      h.header_bytes != (int32_t)hb)
+    return fail(c, VPLBM_EINVAL, "not a snapshot of this library version");
+  if (!same_config(h.cfg, c->cfg) || h.tail_bytes != tb || h.pop_bytes != pb)
+    return fail(c, VPLBM_EINVAL, "snapshot of a lattice with another configuration");
+  if ((h.cur != 0 && h.cur != 1) || h.n_sim < 0 || h.n_sim > effective_max_sim(c->cfg))
+    return fail(c, VPLBM_EINVAL, "corrupt snapshot header");
+  const char *in = static_cast<const char *>(host);
+  VPLBM_CUDA(c, cudaMemcpyAsync(c->ws + c->lay.prev[0], in + hb, tb, cudaMemcpyHostToDevice, c->stream));
+  VPLBM_CUDA(c, cudaMemcpyAsync(c->buf[h.cur], in + hb + tb, pb, cudaMemcpyHostToDevice, c->stream));
+  if (vplbm_status st = sync(c)) return st;
+  c->body_cfg = h.body_cfg;
+  c->body_host = h.body_host;
+  c->region_host = h.region_host;
+  for (int k = 0; k < 3; ++k) c->sim_const[k] = h.sim_const[k];
+  c->steps = h.steps;
+  c->cur = h.cur;
+  c->pre = h.pre != 0;
+  c->n_sim = h.n_sim;
+  c->sim_every = h.sim_every;
+  c->region_slots = h.region_slots;
+  c->pending = false;
+  c->pending_sim = false;
+  c->mask_stale = false;
+  c->has_body = true;
+  drop_graphs(c);
+  ++c->generation;  // batches re-capture their graphs
   return VPLBM_OK;
 }
 
@@ -934,17 +1259,18 @@ vplbm_status vplbm_launch_count(vplbm_ctx *c, int64_t *n) {
 }
 
 vplbm_status vplbm_autotune(vplbm_ctx *c, int32_t trials, int32_t *variant) {
+  Range range_("vplbm_autotune");
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (trials < 1 || trials > 10000) return fail(c, VPLBM_EINVAL, "trials must be in 1 .. 10000");
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "place a body first");
-  // the forms in turn, kTuneRounds times: per form 2 * kGraphPairs untimed
-  // steps (the step graph is captured there), then `trials` timed steps;
+  // the forms in turn, kTuneRounds times: per form kGraphMax untimed steps
+  // (the step graphs are captured there), then `trials` timed steps;
   // each form's fastest round counts
   float t[kBulkVariants];
   for (int r = 0; r < kTuneRounds; ++r)
     for (int v = 0; v < kBulkVariants; ++v) {
       set_variant(c, v);
-      if (vplbm_status st = vplbm_step(c, 2 * kGraphPairs)) return st;
+      if (vplbm_status st = vplbm_step(c, kGraphMax)) return st;
       float ms = 0.f;
       if (vplbm_status st = timed(c->stream, trials, &ms, [&] { return vplbm_step(c, trials); }, c))
         return st;
@@ -973,7 +1299,7 @@ vplbm_status vplbm_bulk_variant(vplbm_ctx *c, int32_t *variant) {
 
 void vplbm_destroy(vplbm_ctx *c) {
   if (!c) return;
-  if (c->graph) cudaGraphExecDestroy(c->graph);
+  drop_graphs(c);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -994,7 +1320,9 @@ struct vplbm_batch {
   std::vector<uint64_t> generations;  // of the contexts when the graph was captured
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
-  cudaGraphExec_t graph = nullptr;  // 2 * kGraphPairs steps of every lattice from buffer 0
+  // graphs[p][k]: 2^k steps of every lattice, each starting from buffer p
+  cudaGraphExec_t graphs[2][kGraphLevels] = {};
+  bool graphs_ready = false;
   std::vector<cudaEvent_t> ev_in;   // each lattice's stream -> the batch stream
   cudaEvent_t ev_out = nullptr;     // the batch stream -> each lattice's stream
   std::vector<cudaStream_t> chain;  // one stream per lattice: the lattices' steps run side by side
@@ -1019,8 +1347,13 @@ vplbm_status batch_ctx_fail(vplbm_status st, int k, const vplbm_ctx *c) {
 }
 
 void batch_drop_graph(vplbm_batch *b) {
-  if (b->graph) cudaGraphExecDestroy(b->graph);
-  b->graph = nullptr;
+  for (auto &row : b->graphs)
+    for (cudaGraphExec_t &g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+  b->graphs_ready = false;
 }
 
 // The lattices share no data, so each runs its steps on a stream of its own
@@ -1043,20 +1376,24 @@ cudaError_t batch_join(vplbm_batch *b, cudaStream_t s) {
   return e;
 }
 
-// Finalizes the lattices' pending force sums, each on its chain.
+// Finalizes the lattices' pending force sums and refreshes the masks of
+// moving bodies, each lattice on its chain.
 cudaError_t batch_flush(vplbm_batch *b, cudaStream_t s) {
   bool any = false;
-  for (vplbm_ctx *c : b->ctxs) any = any || c->pending;
+  for (vplbm_ctx *c : b->ctxs) any = any || c->pending || c->mask_stale;
   if (!any) return cudaSuccess;
   cudaError_t e = batch_fork(b, s);
-  for (size_t q = 0; q < b->ctxs.size() && e == cudaSuccess; ++q)
+  for (size_t q = 0; q < b->ctxs.size() && e == cudaSuccess; ++q) {
     e = flush_forces(b->ctxs[q], b->chain[q]);
+    if (e == cudaSuccess) e = refresh_mask(b->ctxs[q], b->chain[q]);
+  }
   if (e == cudaSuccess) e = batch_join(b, s);
   return e;
 }
 
-// One graph holding 2 * kGraphPairs steps of every lattice, each lattice on
-// its chain, each starting from buffer 0.
+// The batch's step graphs, as ensure_graphs captures them for one lattice:
+// 2^k steps of every lattice, each lattice on its chain, every lattice
+// starting from buffer p, for every length and both p.
 vplbm_status batch_capture(vplbm_batch *b) {
   batch_drop_graph(b);
   if (!b->capture_stream) {
@@ -1065,38 +1402,70 @@ vplbm_status batch_capture(vplbm_batch *b) {
   }
   std::vector<int64_t> launches;
   for (vplbm_ctx *c : b->ctxs) launches.push_back(c->launches);
-  cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return batch_cuda(e, "cudaStreamBeginCapture");
-  e = batch_fork(b, b->capture_stream);
-  for (int k = 0; k < 2 * kGraphPairs && e == cudaSuccess; ++k)
-    for (size_t q = 0; q < b->ctxs.size() && e == cudaSuccess; ++q) {
-      vplbm_ctx *c = b->ctxs[q];
-      e = queue_step(c, b->chain[q], k & 1, false, c->sim_every == 1 && c->n_sim > 0);
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < kGraphLevels; ++k) {
+      cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        batch_drop_graph(b);
+        return batch_cuda(e, "cudaStreamBeginCapture");
+      }
+      e = batch_fork(b, b->capture_stream);
+      std::vector<int> cur;
+      std::vector<char> stale;
+      for (vplbm_ctx *c : b->ctxs) {
+        cur.push_back(c->cur);
+        stale.push_back(c->mask_stale ? 1 : 0);
+        c->cur = (p + (1 << k)) & 1;  // the level the graph ends at, for the end of run work
+      }
+      for (int q = 0; q < (1 << k) && e == cudaSuccess; ++q)
+        for (size_t m = 0; m < b->ctxs.size() && e == cudaSuccess; ++m) {
+          vplbm_ctx *c = b->ctxs[m];
+          e = queue_step(c, b->chain[m], (p + q) & 1, false, c->sim_every == 1 && c->n_sim > 0);
+        }
+      // the graph ends with the forces finalized and the masks refreshed
+      for (size_t m = 0; m < b->ctxs.size() && e == cudaSuccess; ++m) {
+        e = flush_forces(b->ctxs[m], b->chain[m]);
+        if (e == cudaSuccess) e = refresh_mask(b->ctxs[m], b->chain[m]);
+      }
+      if (e == cudaSuccess) e = batch_join(b, b->capture_stream);
+      for (size_t m = 0; m < b->ctxs.size(); ++m) {
+        b->ctxs[m]->launches = launches[m];
+        b->ctxs[m]->cur = cur[m];
+        b->ctxs[m]->mask_stale = stale[m] != 0;
+      }
+      cudaGraph_t g = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
+      if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        batch_drop_graph(b);
+        return batch_cuda(e, "capture of a batch graph");
+      }
+      if (e2 != cudaSuccess) {
+        batch_drop_graph(b);
+        return batch_cuda(e2, "cudaStreamEndCapture");
+      }
+      e = cudaGraphInstantiate(&b->graphs[p][k], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->graphs[p][k] = nullptr;
+        batch_drop_graph(b);
+        return batch_cuda(e, "cudaGraphInstantiate");
+      }
+      // uploaded now, so that the first launch of each does not pay for it
+      e = cudaGraphUpload(b->graphs[p][k], b->stream);
+      if (e != cudaSuccess) {
+        batch_drop_graph(b);
+        return batch_cuda(e, "cudaGraphUpload");
+      }
     }
-  for (size_t q = 0; q < b->ctxs.size() && e == cudaSuccess; ++q)
-    e = flush_forces(b->ctxs[q], b->chain[q]);  // the graph ends finalized
-  if (e == cudaSuccess) e = batch_join(b, b->capture_stream);
-  for (size_t q = 0; q < b->ctxs.size(); ++q) b->ctxs[q]->launches = launches[q];
-  cudaGraph_t g = nullptr;
-  const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
-  if (e != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    return batch_cuda(e, "capture of the batch graph");
-  }
-  if (e2 != cudaSuccess) return batch_cuda(e2, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&b->graph, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    b->graph = nullptr;
-    return batch_cuda(e, "cudaGraphInstantiate");
-  }
+  b->graphs_ready = true;
   b->generations.clear();
   for (vplbm_ctx *c : b->ctxs) b->generations.push_back(c->generation);
   return VPLBM_OK;
 }
 
 bool batch_graph_current(const vplbm_batch *b) {
-  if (!b->graph) return false;
+  if (!b->graphs_ready) return false;
   for (size_t q = 0; q < b->ctxs.size(); ++q)
     if (b->ctxs[q]->generation != b->generations[q]) return false;
   return true;
@@ -1147,6 +1516,7 @@ vplbm_status vplbm_batch_create(vplbm_ctx *const *ctxs, int32_t n, void *cuda_st
 }
 
 vplbm_status vplbm_batch_autotune(vplbm_batch *b, int32_t trials, int32_t *variant) {
+  Range range_("vplbm_batch_autotune");
   if (!b) return batch_fail(VPLBM_EINVAL, "vplbm_batch_autotune: batch is NULL");
   if (trials < 1 || trials > 10000)
     return batch_fail(VPLBM_EINVAL, "vplbm_batch_autotune: trials must be in 1 .. 10000");
@@ -1154,7 +1524,7 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int32_t trials, int32_t *varia
   for (int r = 0; r < kTuneRounds; ++r)
     for (int v = 0; v < kBulkVariants; ++v) {
       for (vplbm_ctx *c : b->ctxs) set_variant(c, v);
-      if (vplbm_status st = vplbm_batch_step(b, 2 * kGraphPairs)) return st;
+      if (vplbm_status st = vplbm_batch_step(b, kGraphMax)) return st;
       float ms = 0.f;
       if (vplbm_status st = timed(b->stream, trials, &ms, [&] { return vplbm_batch_step(b, trials); },
                                   nullptr))
@@ -1170,6 +1540,7 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int32_t trials, int32_t *varia
 }
 
 vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
+  Range range_("vplbm_batch_step");
   if (!b) return batch_fail(VPLBM_EINVAL, "vplbm_batch_step: batch is NULL");
   if (nsteps < 0) return batch_fail(VPLBM_EINVAL, "vplbm_batch_step: nsteps must be >= 0");
   const int n = (int)b->ctxs.size();
@@ -1190,22 +1561,26 @@ vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
   for (vplbm_ctx *c : b->ctxs) graphable = graphable && c->sim_every <= 1;
   int left = nsteps;
   while (left > 0) {
-    bool aligned = graphable && left >= 2 * kGraphPairs;
-    for (vplbm_ctx *c : b->ctxs) aligned = aligned && !c->pre && c->cur == 0;
+    // graphs need every lattice past its first step and all at one parity
+    bool aligned = graphable;
+    for (vplbm_ctx *c : b->ctxs) aligned = aligned && !c->pre && c->cur == b->ctxs[0]->cur;
     if (aligned) {
       // a graph starts with no lattice's force sums pending
       if (const cudaError_t e = batch_flush(b, s); e != cudaSuccess)
         return batch_cuda(e, "vplbm_batch_step: finalizing force sums");
       if (!batch_graph_current(b))
         if (vplbm_status st = batch_capture(b)) return st;
-      const cudaError_t e = cudaGraphLaunch(b->graph, s);
+      const int k = graph_level(left), len = 1 << k;
+      const cudaError_t e = cudaGraphLaunch(b->graphs[b->ctxs[0]->cur][k], s);
       if (e != cudaSuccess) return batch_cuda(e, "vplbm_batch_step: cudaGraphLaunch");
       for (vplbm_ctx *c : b->ctxs) {
-        c->launches += 4 * kGraphPairs + 1;
-        c->steps += 2 * kGraphPairs;
+        c->launches += 2 * len + 1 + (c->body_host.moving ? 1 : 0);
+        c->steps += len;
+        c->cur ^= len & 1;
         c->pending = false;
+        c->mask_stale = false;
       }
-      left -= 2 * kGraphPairs;
+      left -= len;
       continue;
     }
     if (const cudaError_t e = batch_fork(b, s); e != cudaSuccess)

@@ -64,28 +64,33 @@ __global__ void init_kernel(Lattice L, const BodyState *body, const uint8_t *chi
   }
 }
 
+// Read-back kernels cover the rows j0 .. j0 + rows - 1 and write them
+// compactly, [rows][nx] per output plane, so that the host read-backs can
+// stage a few rows at a time.
+
+// planes a0 .. a0 + na - 1 of the pre-collision populations f = h + E
 template <typename S, bool kGather>
 __global__ void get_f_kernel(Lattice L, const S *buf, const typename Store<S>::T *prev,
-                             double *out) {
+                             double *out, int a0, int na, int j0, int rows) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t n = (int64_t)L.nx * L.ny;
+  const int64_t n = (int64_t)L.nx * rows;
   if (k >= n) return;
-  const int i = (int)(k % L.nx), j = (int)(k / L.nx);
+  const int i = (int)(k % L.nx), j = j0 + (int)(k / L.nx);
 #pragma unroll
   for (int a = 0; a < 9; ++a)
-    out[a * n + k] = (double)pre_pop<S, kGather>(buf, prev, L, a, i, j) + L.E[a];
+    if (a >= a0 && a < a0 + na)
+      out[(a - a0) * n + k] = (double)pre_pop<S, kGather>(buf, prev, L, a, i, j) + L.E[a];
 }
 
 // macroscopic fields of Eqs. updatestep and updatestepm, FP64
 template <typename S, bool kGather>
 __global__ void get_fields_kernel(Lattice L, const S *buf, const typename Store<S>::T *prev,
-                                  const uint8_t *chi,
-                                  const BodyState *body, double half_pen, double *rho_o,
-                                  double *ux_o, double *uy_o) {
+                                  const uint8_t *chi, const BodyState *body, double half_pen,
+                                  double *rho_o, double *ux_o, double *uy_o, int j0, int rows) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t n = (int64_t)L.nx * L.ny;
+  const int64_t n = (int64_t)L.nx * rows;
   if (k >= n) return;
-  const int i = (int)(k % L.nx), j = (int)(k / L.nx);
+  const int i = (int)(k % L.nx), j = j0 + (int)(k / L.nx);
   double rho = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
@@ -134,39 +139,39 @@ __global__ void set_prev_kernel(Lattice L, const double *f, T *prev) {
   prev[2 * L.ny + j] = (T)(f[7 * n + k] - L.E[7]);
 }
 
-__global__ void get_mask_kernel(Lattice L, const uint8_t *chi, uint8_t *out) {
+__global__ void get_mask_kernel(Lattice L, const uint8_t *chi, uint8_t *out, int j0, int rows) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= (int64_t)L.nx * L.ny) return;
-  const int i = (int)(k % L.nx), j = (int)(k / L.nx);
+  if (k >= (int64_t)L.nx * rows) return;
+  const int i = (int)(k % L.nx), j = j0 + (int)(k / L.nx);
   out[k] = chi[(int64_t)j * L.pitch + i] & kSolid;
 }
 
 template <typename S>
 cudaError_t get_f_t(bool gather, const Lattice &L, const void *buf, const void *prev_v,
-                    double *out, cudaStream_t s) {
+                    double *out, int a0, int na, int j0, int rows, cudaStream_t s) {
   using T = typename Store<S>::T;
   const T *prev = static_cast<const T *>(prev_v);
-  const int g = blocks_for((int64_t)L.nx * L.ny);
+  const int g = blocks_for((int64_t)L.nx * rows);
   if (gather)
-    get_f_kernel<S, true><<<g, kAuxThreads, 0, s>>>(L, (const S *)buf, prev, out);
+    get_f_kernel<S, true><<<g, kAuxThreads, 0, s>>>(L, (const S *)buf, prev, out, a0, na, j0, rows);
   else
-    get_f_kernel<S, false><<<g, kAuxThreads, 0, s>>>(L, (const S *)buf, prev, out);
+    get_f_kernel<S, false><<<g, kAuxThreads, 0, s>>>(L, (const S *)buf, prev, out, a0, na, j0, rows);
   return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t get_fields_t(bool gather, const Lattice &L, const void *buf, const void *prev_v,
                          const uint8_t *chi, const BodyState *body, double half_pen, double *rho,
-                         double *ux, double *uy, cudaStream_t s) {
+                         double *ux, double *uy, int j0, int rows, cudaStream_t s) {
   using T = typename Store<S>::T;
   const T *prev = static_cast<const T *>(prev_v);
-  const int g = blocks_for((int64_t)L.nx * L.ny);
+  const int g = blocks_for((int64_t)L.nx * rows);
   if (gather)
-    get_fields_kernel<S, true>
-        <<<g, kAuxThreads, 0, s>>>(L, (const S *)buf, prev, chi, body, half_pen, rho, ux, uy);
+    get_fields_kernel<S, true><<<g, kAuxThreads, 0, s>>>(L, (const S *)buf, prev, chi, body,
+                                                         half_pen, rho, ux, uy, j0, rows);
   else
-    get_fields_kernel<S, false>
-        <<<g, kAuxThreads, 0, s>>>(L, (const S *)buf, prev, chi, body, half_pen, rho, ux, uy);
+    get_fields_kernel<S, false><<<g, kAuxThreads, 0, s>>>(L, (const S *)buf, prev, chi, body,
+                                                          half_pen, rho, ux, uy, j0, rows);
   return cudaGetLastError();
 }
 
@@ -204,26 +209,33 @@ cudaError_t launch_init(int dtype, const Lattice &L, const BodyState *body, cons
 }
 
 cudaError_t launch_get_f(int dtype, bool gather, const Lattice &L, const void *buf,
-                         const void *prev, double *out, cudaStream_t s) {
+                         const void *prev, double *out, int a0, int na, int j0, int rows,
+                         cudaStream_t s) {
+  if (rows <= 0 || na <= 0) return cudaSuccess;
   switch (dtype) {
-    case VPLBM_F64: return get_f_t<double>(gather, L, buf, prev, out, s);
-    case VPLBM_F32: return get_f_t<float>(gather, L, buf, prev, out, s);
-    case VPLBM_F16_OFS: return get_f_t<__half>(gather, L, buf, prev, out, s);
-    case VPLBM_BF16_OFS: return get_f_t<__nv_bfloat16>(gather, L, buf, prev, out, s);
+    case VPLBM_F64: return get_f_t<double>(gather, L, buf, prev, out, a0, na, j0, rows, s);
+    case VPLBM_F32: return get_f_t<float>(gather, L, buf, prev, out, a0, na, j0, rows, s);
+    case VPLBM_F16_OFS: return get_f_t<__half>(gather, L, buf, prev, out, a0, na, j0, rows, s);
+    case VPLBM_BF16_OFS: return get_f_t<__nv_bfloat16>(gather, L, buf, prev, out, a0, na, j0, rows, s);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_get_fields(int dtype, bool gather, const Lattice &L, const void *buf,
                               const void *prev, const uint8_t *chi, const BodyState *body,
-                              double half_pen, double *rho, double *ux, double *uy,
-                              cudaStream_t s) {
+                              double half_pen, double *rho, double *ux, double *uy, int j0,
+                              int rows, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
   switch (dtype) {
-    case VPLBM_F64: return get_fields_t<double>(gather, L, buf, prev, chi, body, half_pen, rho, ux, uy, s);
-    case VPLBM_F32: return get_fields_t<float>(gather, L, buf, prev, chi, body, half_pen, rho, ux, uy, s);
-    case VPLBM_F16_OFS: return get_fields_t<__half>(gather, L, buf, prev, chi, body, half_pen, rho, ux, uy, s);
+    case VPLBM_F64:
+      return get_fields_t<double>(gather, L, buf, prev, chi, body, half_pen, rho, ux, uy, j0, rows, s);
+    case VPLBM_F32:
+      return get_fields_t<float>(gather, L, buf, prev, chi, body, half_pen, rho, ux, uy, j0, rows, s);
+    case VPLBM_F16_OFS:
+      return get_fields_t<__half>(gather, L, buf, prev, chi, body, half_pen, rho, ux, uy, j0, rows, s);
     case VPLBM_BF16_OFS:
-      return get_fields_t<__nv_bfloat16>(gather, L, buf, prev, chi, body, half_pen, rho, ux, uy, s);
+      return get_fields_t<__nv_bfloat16>(gather, L, buf, prev, chi, body, half_pen, rho, ux, uy, j0,
+                                         rows, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -252,8 +264,10 @@ cudaError_t launch_set_prev(int dtype, const Lattice &L, const double *f, void *
   return cudaGetLastError();
 }
 
-cudaError_t launch_get_mask(const Lattice &L, const uint8_t *chi, uint8_t *out, cudaStream_t s) {
-  get_mask_kernel<<<blocks_for((int64_t)L.nx * L.ny), kAuxThreads, 0, s>>>(L, chi, out);
+cudaError_t launch_get_mask(const Lattice &L, const uint8_t *chi, uint8_t *out, int j0, int rows,
+                            cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  get_mask_kernel<<<blocks_for((int64_t)L.nx * rows), kAuxThreads, 0, s>>>(L, chi, out, j0, rows);
   return cudaGetLastError();
 }
 

@@ -27,10 +27,6 @@ constexpr int kDoubles = 8;  // per point: dx, dy, nx, ny, S, then Fx, Fy, T
 constexpr int kHeader = 8;
 static __device__ __align__(256) double g_scratch[kHeader + kMaxPts * kDoubles];
 
-// device address of g_scratch, per device, taken once
-constexpr int kMaxDevices = 64;
-double *g_addr[kMaxDevices] = {nullptr};
-
 // SIM term of one point from FP64 pre-collision populations (the same
 // definition as the library's step: nearest node or both nodes of an exact
 // tie, walk along the lattice direction closest to the normal to the first
@@ -140,24 +136,28 @@ extern "C" vplbm_status vplbm_sim_force_static(const vplbm_config *cfg, const do
     return static_fail(VPLBM_EINVAL, "vplbm_sim_force_static: NULL argument");
   if (cfg->nx < 3 || cfg->ny < 3 || !(cfg->tau_plus > 0.5))
     return static_fail(VPLBM_EINVAL, "vplbm_sim_force_static: bad lattice size or tau_plus");
+  if (cfg->sim_order != 0)
+    return static_fail(VPLBM_EINVAL, "vplbm_sim_force_static: only the stress copied from the "
+                                     "sampled node (sim_order 0) is evaluated here");
   if (n_pts < 1 || n_pts > kMaxPts)
     return static_fail(VPLBM_EINVAL, "vplbm_sim_force_static: " + std::to_string(n_pts) +
                                          " points; this entry point holds at most " +
                                          std::to_string(kMaxPts));
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return static_fail(VPLBM_ECUDA, "vplbm_sim_force_static: no usable current device");
-  // once per device, with that device current: the device address of the
-  // scratch array (its name in host code is not a device address)
-  if (!g_addr[dev]) {
+  // the device address of the scratch array on the current device (its name
+  // in host code is not a device address).  Taken on every call, with the
+  // device current: cudaGetSymbolAddress allocates nothing, and a context
+  // torn down and re-created between calls (a device reset by the embedding
+  // application) gets the array's new address.  On the first call on a
+  // device it also loads this library's device code there.
+  double *scratch = nullptr;
+  {
     void *ptr = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
     if (e != cudaSuccess || !ptr)
       return static_fail(VPLBM_ECUDA, std::string("vplbm_sim_force_static: cudaGetSymbolAddress: ") +
                                           cudaGetErrorString(e));
-    g_addr[dev] = static_cast<double *>(ptr);
+    scratch = static_cast<double *>(ptr);
   }
-  double *scratch = g_addr[dev];
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   // the points into the scratch rows (columns 0..4), the header cleared
   cudaError_t e = cudaMemsetAsync(scratch, 0, kHeader * sizeof(double), s);

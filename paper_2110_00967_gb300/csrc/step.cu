@@ -7,10 +7,12 @@
 //     conditions of Sec. 3.1/3.2), and the tiles of the force region around
 //     the body (penalized nodes and the MEM link terms of Eq. MMEL /
 //     Eq. fluidtorque).  Its SIM and region blocks add their force terms into
-//     exact fixed-point sums.  For a moving body they take a ticket and the
-//     last of them records the step's forces, applies the FP64 rigid-body
-//     update (Eqs. dep1, theta2) and re-rasterises the mask; for a fixed body
-//     one extra block of the next step's launch records them.
+//     exact fixed-point sums.  For a moving body the region tiles rasterise
+//     the mask of the body's current position themselves (each tile with a
+//     one-node halo), the blocks take a ticket and the last of them records
+//     the step's forces and applies the FP64 rigid-body update (Eqs. dep1,
+//     theta2); for a fixed body one extra block of the next step's launch
+//     records them.
 //   * the bulk kernel: every other node -- pull streaming (Eq. eqBd) and the
 //     BGK/TRT collision (Eq. TRT) of fluid nodes whose sources all lie inside
 //     the lattice; no mask, no side conditions, no forces.  It comes in
@@ -122,17 +124,26 @@ __device__ __forceinline__ void node_stress(const S *buf, const typename Store<S
   sig[2] = -drho / (T)3 - c.sim_s * pyy;
 }
 
+// mask byte of node (i, j) (inside the lattice) as SIM and MEM see it: chi,
+// or for a moving body the predicate of Eq. fcar on the current body, since
+// the force-region tiles rewrite chi during the step
+__device__ __forceinline__ uint8_t solid_at(const StepArgs &p, int i, int j) {
+  if (p.raster) return body_contains(*p.body_src, i, j) ? kSolid : (uint8_t)0;
+  return p.chi[(int64_t)j * p.L.pitch + i];
+}
+
 // first fluid node of q_k = (qi, qj) + k c_a, k = 0..3, inside the lattice
 // (the four mask bytes are loaded together)
-__device__ __forceinline__ bool sim_walk(const Lattice &L, const uint8_t *chi, int a, int qi,
-                                         int qj, int &oi, int &oj) {
+__device__ __forceinline__ bool sim_walk(const StepArgs &p, int a, int qi, int qj, int &oi,
+                                         int &oj) {
+  const Lattice &L = p.L;
   uint8_t m[4];
   bool in[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int ii = qi + k * cx_of(a), jj = qj + k * cy_of(a);
     in[k] = ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny;
-    m[k] = in[k] ? chi[(int64_t)jj * L.pitch + ii] : (uint8_t)kSolid;
+    m[k] = in[k] ? solid_at(p, ii, jj) : (uint8_t)kSolid;
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -179,7 +190,7 @@ __device__ __noinline__ FixAcc<typename Store<S>::T> sim_point(const StepArgs &p
   for (int u = 0; u < ncy && ok; ++u)
     for (int v = 0; v < ncx && ok; ++v) {
       int qi, qj;
-      if (!sim_walk(p.L, p.chi, sp.dir, (int)rx - v, (int)ry - u, qi, qj)) {
+      if (!sim_walk(p, sp.dir, (int)rx - v, (int)ry - u, qi, qj)) {
         ok = false;
         break;
       }
@@ -190,8 +201,7 @@ __device__ __noinline__ FixAcc<typename Store<S>::T> sim_point(const StepArgs &p
         // first order: extrapolated to the point along the direction from
         // the next node, where that node is fluid and inside the lattice
         const int ni = qi + cx_of(sp.dir), nj = qj + cy_of(sp.dir);
-        if (ni >= 0 && ni < p.L.nx && nj >= 0 && nj < p.L.ny &&
-            !(p.chi[(int64_t)nj * p.L.pitch + ni] & kSolid)) {
+        if (ni >= 0 && ni < p.L.nx && nj >= 0 && nj < p.L.ny && !(solid_at(p, ni, nj) & kSolid)) {
           T s3n[3];
           node_stress<S, kGather>(buf, prev, p.L, Consts<T>(p), ni, nj, s3n);
           const int c2 = cx_of(sp.dir) * cx_of(sp.dir) + cy_of(sp.dir) * cy_of(sp.dir);
@@ -223,6 +233,45 @@ __device__ __noinline__ FixAcc<typename Store<S>::T> sim_point(const StepArgs &p
 }
 
 // ---------------------------------------------------------------------------
+// the mask of a moving body, rasterised tile by tile (Eq. fcar)
+// ---------------------------------------------------------------------------
+// Solid bits of one tile and a one-node halo around it: the predicate of
+// Eq. fcar on the body at the step's time level, evaluated by the tile's own
+// block, so that no single block re-rasterises the body between steps.
+struct TileMask {
+  uint8_t s[kTileY + 2][kTileX + 2];
+};
+
+__device__ __forceinline__ void tile_solid(const StepArgs &p, int ti, int tj, TileMask &tm) {
+  const Lattice &L = p.L;
+  const int tid = threadIdx.y * kTileX + threadIdx.x;
+  for (int q = tid; q < (kTileY + 2) * (kTileX + 2); q += kThreads) {
+    const int hx = q % (kTileX + 2), hy = q / (kTileX + 2);
+    int gi = ti * kTileX + hx - 1, gj = tj * kTileY + hy - 1;
+    // halo nodes across a periodic side are the nodes there; beyond another
+    // side they are never a neighbour (neighbour() gives false)
+    if (L.bc[0] == VPLBM_PERIODIC) gi = gi < 0 ? gi + L.nx : (gi >= L.nx ? gi - L.nx : gi);
+    if (L.bc[2] == VPLBM_PERIODIC) gj = gj < 0 ? gj + L.ny : (gj >= L.ny ? gj - L.ny : gj);
+    const bool in = gi >= 0 && gi < L.nx && gj >= 0 && gj < L.ny;
+    tm.s[hy][hx] = (in && body_contains(*p.body_src, gi, gj)) ? kSolid : (uint8_t)0;
+  }
+}
+
+// mask byte (solid bit and interface bit) of the tile node (tx, ty) at (i, j)
+__device__ __forceinline__ uint8_t tile_mask_byte(const Lattice &L, const TileMask &tm, int i,
+                                                  int j, int tx, int ty) {
+  const uint8_t self = tm.s[ty + 1][tx + 1];
+  bool iface = false;
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    int ni, nj;
+    if (neighbour(L, a, i, j, ni, nj) && tm.s[ty + 1 + cy_of(a)][tx + 1 + cx_of(a)] != self)
+      iface = true;
+  }
+  return (uint8_t)(self | (iface ? kInterface : 0));
+}
+
+// ---------------------------------------------------------------------------
 // MEM (Sec. 2.3.1)
 // ---------------------------------------------------------------------------
 
@@ -231,10 +280,11 @@ __device__ __noinline__ FixAcc<typename Store<S>::T> sim_point(const StepArgs &p
 // the solid end subtracts its own (c_a - u_Gamma) f~_a, with x_Gamma the link
 // midpoint and u_Gamma the rigid velocity there; torques about the reference
 // point (Eq. fluidtorque).  f~ = h~ + E is split so that the E parts, which
-// cancel in pairs around a fixed body, are rounded exactly.
+// cancel in pairs around a fixed body, are rounded exactly.  The neighbours'
+// phases come from chi, or from the tile's mask when it rasterises its own.
 template <typename T>
 __device__ __forceinline__ void mem_terms(const StepArgs &p, const T (&o)[9], int i, int j,
-                                          uint8_t m, FixAcc<T> &acc) {
+                                          uint8_t m, const TileMask *tm, FixAcc<T> &acc) {
   const Lattice &L = p.L;
   const BodyRef<T> b(*p.body_src);
   const bool solid = m & kSolid;
@@ -243,7 +293,8 @@ __device__ __forceinline__ void mem_terms(const StepArgs &p, const T (&o)[9], in
   for (int a = 1; a < 9; ++a) {
     int ni, nj;
     if (!neighbour(L, a, i, j, ni, nj)) continue;
-    const bool nsolid = p.chi[(int64_t)nj * L.pitch + ni] & kSolid;
+    const bool nsolid = tm ? (tm->s[threadIdx.y + 1 + cy_of(a)][threadIdx.x + 1 + cx_of(a)] & kSolid)
+                           : (p.chi[(int64_t)nj * L.pitch + ni] & kSolid);
     if (nsolid == solid) continue;
     const T rx = ((T)i - b.xg) + (T)(0.5 * cx_of(a));
     const T ry = ((T)j - b.yg) + (T)(0.5 * cy_of(a));
@@ -281,40 +332,6 @@ __device__ void rigid_update(BodyState &b, const double F[3]) {
   b.yg += 0.5 * (u0y + b.uy);
   b.theta += 0.5 * (w0 + b.omega);
   body_sync_f32(b);
-}
-
-// Re-rasterise the disk mask inside the box covering the old and the new
-// position, then refresh the interface bits one node wider.
-__device__ void tail_reraster(const StepArgs &p, const BodyState &old_b, const BodyState &new_b) {
-  const Lattice &L = p.L;
-  const double r = 0.5 * new_b.length;
-  const int i0 = max(0, (int)floor(fmin(old_b.xg, new_b.xg) - r) - 2);
-  const int i1 = min(L.nx - 1, (int)ceil(fmax(old_b.xg, new_b.xg) + r) + 2);
-  const int j0 = max(0, (int)floor(fmin(old_b.yg, new_b.yg) - r) - 2);
-  const int j1 = min(L.ny - 1, (int)ceil(fmax(old_b.yg, new_b.yg) + r) + 2);
-  const int w = i1 - i0 + 1, h = j1 - j0 + 1;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
-  for (int k = tid; k < w * h; k += nt) {
-    const int i = i0 + k % w, j = j0 + k / w;
-    p.chi[(int64_t)j * L.pitch + i] = body_contains(new_b, i, j) ? kSolid : 0;
-  }
-  __syncthreads();
-  const int a0 = max(0, i0 - 1), a1 = min(L.nx - 1, i1 + 1);
-  const int b0 = max(0, j0 - 1), b1 = min(L.ny - 1, j1 + 1);
-  const int w2 = a1 - a0 + 1, h2 = b1 - b0 + 1;
-  for (int k = tid; k < w2 * h2; k += nt) {
-    const int i = a0 + k % w2, j = b0 + k / w2;
-    const uint8_t self = p.chi[(int64_t)j * L.pitch + i] & kSolid;
-    bool iface = false;
-#pragma unroll
-    for (int a = 1; a < 9; ++a) {
-      int ni, nj;
-      if (neighbour(L, a, i, j, ni, nj) && ((p.chi[(int64_t)nj * L.pitch + ni] & kSolid) != self))
-        iface = true;
-    }
-    // only bit 1 changes here, the solid bits other threads read stay put
-    p.chi[(int64_t)j * L.pitch + i] = (uint8_t)(self | (iface ? kInterface : 0));
-  }
 }
 
 // Force bookkeeping of a step whose tail was deferred (a fixed body): its
@@ -418,8 +435,6 @@ __device__ void tail(const StepArgs &p, const ForceRegion &reg) {
     reinterpret_cast<unsigned long long *>(p.body_dst)[tid - 32] =
         reinterpret_cast<const unsigned long long *>(&new_b)[tid - 32];
   __syncthreads();
-  if (old_b.moving && (new_b.xg != old_b.xg || new_b.yg != old_b.yg)) tail_reraster(p, old_b, new_b);
-  __syncthreads();
   if (tid < kAccWords) p.acc[tid] = 0ull;
   __syncthreads();
   if (tid == 0) {
@@ -432,13 +447,42 @@ __device__ void tail(const StepArgs &p, const ForceRegion &reg) {
 // node update
 // ---------------------------------------------------------------------------
 
+// Coefficients 3 w_a of the odd (momentum-carrying) part of the equilibrium
+// and of the forcing term, for the axis directions (k1 = 3 w_1 = 1/3) and the
+// diagonals (k2 = 3 w_5 = 1/12).  In the compute type they are chosen with
+// 2 k1 + 4 k2 = 1 exactly, so that the odd equilibrium carries exactly the
+// node's momentum: with the rounded weights 1/9 and 1/36 of FP32 (both
+// 7.45e-9 too large) every collision would add 7.45e-9 s- of the momentum
+// offset, a bias that compounds step after step.
+template <typename T>
+struct OddW;
+template <>
+struct OddW<double> {
+  static constexpr double k1 = 1.0 / 3.0;
+  static constexpr double k2 = (1.0 - 2.0 * (1.0 / 3.0)) / 4.0;  // exact: 2 k1 + 4 k2 = 1
+};
+template <>
+struct OddW<float> {
+  static constexpr float k1 = 0x1.555556p-2f;  // 1/3 rounded
+  static constexpr float k2 = 0x1.555554p-4f;  // (1 - 2 k1) / 4, exactly
+};
+template <typename T>
+__device__ __forceinline__ constexpr T odd_w(int a) {
+  return a <= 4 ? OddW<T>::k1 : OddW<T>::k2;
+}
+
 // BGK/TRT collision with the forcing term (Eq. TRT) of one node, into o.
 // The equilibrium enters through its offset heq = feq(rho, u) - E, written
 // with the small quantities drho = rho - 1 and du = u - u_ref only:
 // heq_a = w_a [drho (1 + Q_a(u)) + Q_a(u) - Q_a(u_ref)],
 // Q_a(u) = 3 c.u + 4.5 (c.u)^2 - 1.5 |u|^2, split into its even and odd parts
 // for TRT.  kForce = false drops the forcing term (G = 0: a fluid node
-// without body force).
+// without body force).  The rest population takes what the moving
+// populations' even parts give up, o_0 = h_0 - sum_{a>0} (even change of a):
+// equal to the relaxation of h_0 towards heq_0 (plus F_0) in exact
+// arithmetic, and conserving mass exactly up to the rounding of that sum,
+// where rounded weights would make the collision a mass source proportional
+// to rho - 1.
 template <typename T, bool kForce>
 __device__ __forceinline__ void collide(const T (&h)[9], T drho, T dux, T duy, T gx, T gy,
                                         const Consts<T> &c, T (&o)[9]) {
@@ -446,24 +490,19 @@ __device__ __forceinline__ void collide(const T (&h)[9], T drho, T dux, T duy, T
   const T uu = ux * ux + uy * uy;
   const T dsu = dux * (ux + c.urx) + duy * (uy + c.ury);  // |u|^2 - |u_ref|^2
   const T ug = kForce ? ux * gx + uy * gy : (T)0;
-  {
-    const T w0 = (T)w_of(0);
-    const T heq0 = w0 * (drho * ((T)1 - (T)1.5 * uu) - (T)1.5 * dsu);
-    T r = h[0] - c.s_plus * (h[0] - heq0);
-    if (kForce) r += c.a_plus * (w0 * ((T)-3 * ug));
-    o[0] = r;
-  }
+  T even = 0;  // sum over the pairs of the even change of one population
 #pragma unroll
   for (int a = 1; a <= 6; ++a) {
     if (a == 3 || a == 4) continue;
     const int b = opp_of(a);
     const T w = (T)w_of(a);
+    const T k = odd_w<T>(a);
     const T cu = (T)cx_of(a) * ux + (T)cy_of(a) * uy;
     const T cdu = (T)cx_of(a) * dux + (T)cy_of(a) * duy;
     const T csu = cu + ((T)cx_of(a) * c.urx + (T)cy_of(a) * c.ury);
     const T heqp = w * (drho * ((T)1 + (T)4.5 * cu * cu - (T)1.5 * uu) + (T)4.5 * cdu * csu -
                         (T)1.5 * dsu);
-    const T heqm = w * (T)3 * (drho * cu + cdu);
+    const T heqm = k * (drho * cu + cdu);
     const T hp = (T)0.5 * (h[a] + h[b]);
     const T hm = (T)0.5 * (h[a] - h[b]);
     T dp = -c.s_plus * (hp - heqp);
@@ -471,11 +510,13 @@ __device__ __forceinline__ void collide(const T (&h)[9], T drho, T dux, T duy, T
     if (kForce) {
       const T cg = (T)cx_of(a) * gx + (T)cy_of(a) * gy;
       dp += c.a_plus * (w * ((T)9 * cu * cg - (T)3 * ug));
-      dm += c.a_minus * (w * (T)3 * cg);
+      dm += c.a_minus * (k * cg);
     }
+    even += dp;
     o[a] = h[a] + dp + dm;
     o[b] = h[b] + dp - dm;
   }
+  o[0] = h[0] - (T)2 * even;
 }
 
 // Moments, penalized velocity and force density of one node (Eqs. updatestep
@@ -503,13 +544,19 @@ __device__ __forceinline__ bool update_node(const T (&h)[9], uint8_t m, int i, i
       solid_velocity<T>(*body, i, j, usx, usy);
       const T k = cst.half_pen;
       const T den = rho + k * rho;
-      // u - u_ref = (j + k rho u_s)/(rho (1 + k)) - u_ref
-      dux = (djx - drho * cst.urx + k * rho * (usx - cst.urx)) / den;
-      duy = (djy - drho * cst.ury + k * rho * (usy - cst.ury)) / den;
+      // the momentum defect j - rho u_s, from the offsets' first moment
+      const T defx = djx - drho * usx + (cst.urx - usx);
+      const T defy = djy - drho * usy + (cst.ury - usy);
+      // u - u_ref = (j + k rho u_s)/(rho (1 + k)) - u_ref, written as
+      // (u_s - u_ref) + (j - rho u_s)/(rho (1 + k)): the large part is exact
+      // and the small one keeps its relative precision (k rho u_s alone
+      // would carry an FP32 rounding of 1e-3 into the division by k rho)
+      dux = (usx - cst.urx) + defx / den;
+      duy = (usy - cst.ury) + defy / den;
       // G = -(chi/eta)(j - rho u_s)/(1 + k)
       const T pen = (T)2 * k;
-      pen_x = -pen * (djx - drho * usx + (cst.urx - usx)) / ((T)1 + k);
-      pen_y = -pen * (djy - drho * usy + (cst.ury - usy)) / ((T)1 + k);
+      pen_x = -pen * defx / ((T)1 + k);
+      pen_y = -pen * defy / ((T)1 + k);
       gx += pen_x;
       gy += pen_y;
     } else {
@@ -540,7 +587,7 @@ __device__ __forceinline__ void edge_pops(const S *src, const typename Store<S>:
 // an interface node of the force region.
 template <typename S, bool kGather>
 __device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bool in_reg,
-                                             FixAcc<typename Store<S>::T> &acc,
+                                             const TileMask *tm, FixAcc<typename Store<S>::T> &acc,
                                              FixAcc<typename Store<S>::T> &vol) {
   using T = typename Store<S>::T;
   const Lattice &L = p.L;
@@ -563,12 +610,20 @@ __device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bo
     pd[1 * L.ny + j] = h[6];
     pd[2 * L.ny + j] = h[7];
   }
-  const uint8_t m = p.chi[node];
+  uint8_t m;
+  if (tm) {
+    // a moving body's tile: its mask byte from the tile's predicate, kept in
+    // chi for the read-backs
+    m = tile_mask_byte(L, *tm, i, j, threadIdx.x, threadIdx.y);
+    p.chi[node] = m;
+  } else {
+    m = p.chi[node];
+  }
   T o[9], pen_x, pen_y;
   const bool bad = update_node<T>(h, m, i, j, L, p.body_src, Consts<T>(p), o, pen_x, pen_y);
 #pragma unroll
   for (int a = 0; a < 9; ++a) Store<S>::st(dst + (int64_t)a * L.plane + node, o[a]);
-  if (in_reg && (m & kInterface)) mem_terms<T>(p, o, i, j, m, acc);
+  if (in_reg && (m & kInterface)) mem_terms<T>(p, o, i, j, m, tm, acc);
   if (in_reg && (m & kSolid)) {
     // volume integral (Eq. Angotforce, reading R19): the penalization force
     // on the fluid, reversed, and its moment about the reference point
@@ -595,6 +650,7 @@ template <typename S, bool kGather>
 __global__ void __launch_bounds__(kThreads, kSpecialMinBlocks<S>) special_kernel(const StepArgs p) {
   using T = typename Store<S>::T;
   __shared__ int is_last;
+  __shared__ TileMask tmask;
   const Lattice &L = p.L;
   const int tid = threadIdx.y * kTileX + threadIdx.x;
   const ForceRegion reg = *p.reg_src;
@@ -628,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, kSpecialMinBlocks<S>) special_kernel
       const bool in_reg = ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1;
       if (!in_reg) {
         FixAcc<T> unused, unused_vol;
-        bad = special_node<S, kGather>(p, i, j, false, unused, unused_vol);
+        bad = special_node<S, kGather>(p, i, j, false, nullptr, unused, unused_vol);
       }
     }
     if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(p.status, kStatusUnstable);
@@ -650,9 +706,16 @@ __global__ void __launch_bounds__(kThreads, kSpecialMinBlocks<S>) special_kernel
     const bool in_reg = ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1;
     const int i = ti * kTileX + threadIdx.x;
     const int j = tj * kTileY + threadIdx.y;
+    // a moving body: the region tiles rasterise its mask at this level
+    const bool raster = p.raster && in_reg;  // uniform over the block
+    if (raster) {
+      tile_solid(p, ti, tj, tmask);
+      __syncthreads();
+    }
     bool bad = false;
     FixAcc<T> acc, vol;
-    if (i < L.nx && j < L.ny) bad = special_node<S, kGather>(p, i, j, in_reg, acc, vol);
+    if (i < L.nx && j < L.ny)
+      bad = special_node<S, kGather>(p, i, j, in_reg, raster ? &tmask : nullptr, acc, vol);
     if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(p.status, kStatusUnstable);
     if (!in_reg) return;  // uniform over the block
     warp_add(acc, p.acc, 0);
@@ -755,12 +818,16 @@ __device__ __forceinline__ F2 vrcp(F2 a) { return vpair(__frcp_rn(a.v.x), __frcp
 __device__ __forceinline__ float vlo(F2 a) { return a.v.x; }
 __device__ __forceinline__ float vhi(F2 a) { return a.v.y; }
 
-// The collision of collide() for two nodes, with the relaxation rates and
-// weights folded into the coefficients: for each pair (a, opp(a))
+// The collision of collide() for two nodes, with the relaxation rate and
+// weights folded into the even part's coefficients: for each pair
+// (a, opp(a))
 //   s+ heq+ = s+ w K + 4.5 s+ w X,  X = drho (c.u)^2 + (c.du)(c.u + c.u_ref),
-//   s- heq- = 3 s- w (drho c.u + c.du),
 //   K = drho (1 - 1.5 |u|^2) - 1.5 (|u|^2 - |u_ref|^2),
-// the same terms as heq_a = w_a [drho (1 + Q_a(u)) + Q_a(u) - Q_a(u_ref)].
+// the same terms as heq_a = w_a [drho (1 + Q_a(u)) + Q_a(u) - Q_a(u_ref)].  The
+// odd part keeps collide()'s form -s- (h- - k (drho c.u + c.du)) with the
+// coefficients k of odd_w (its momentum is then exact: a folded s- k would
+// round differently from s-), and the rest population takes the even
+// changes' remainder as in collide().
 template <typename V, typename T, bool kForce>
 __device__ __forceinline__ void collide2(const V (&h)[9], V drho, V dux, V duy, V gx, V gy,
                                          const Consts<T> &c, V (&o)[9]) {
@@ -772,19 +839,14 @@ __device__ __forceinline__ void collide2(const V (&h)[9], V drho, V dux, V duy, 
   const V K = vfma(m15, dsu, vmul(drho, vfma(m15, uu, vsplat((T)1))));
   V ug{};
   if (kForce) ug = vfma(ux, gx, vmul(uy, gy));
-  {
-    const T w0 = (T)w_of(0);
-    const V heq0 = vmul(vsplat(w0), K);
-    V r = vfma(vsplat(-c.s_plus), vsub(h[0], heq0), h[0]);
-    if (kForce) r = vfma(vsplat(c.a_plus * w0 * (T)-3), ug, r);
-    o[0] = r;
-  }
-  const V nsph = vsplat((T)-0.5 * c.s_plus), nsmh = vsplat((T)-0.5 * c.s_minus);
+  const V nsph = vsplat((T)-0.5 * c.s_plus), nsm = vsplat(-c.s_minus), half = vsplat((T)0.5);
+  V even = vsplat((T)0);
 #pragma unroll
   for (int a = 1; a <= 6; ++a) {
     if (a == 3 || a == 4) continue;
     const int b = opp_of(a);
     const T w = (T)w_of(a);
+    const V k = vsplat(odd_w<T>(a));
     // c.u, c.du for the four directions 1 (1,0), 2 (0,1), 5 (1,1), 6 (-1,1)
     V cu, cdu;
     if (a == 1) {
@@ -804,9 +866,9 @@ __device__ __forceinline__ void collide2(const V (&h)[9], V drho, V dux, V duy, 
     const V dc = vmul(drho, cu);
     const V X = vfma(dc, cu, vmul(cdu, csu));
     const V P = vfma(vsplat((T)4.5 * c.s_plus * w), X, vmul(vsplat(c.s_plus * w), K));
-    const V Q = vmul(vsplat((T)3 * c.s_minus * w), vadd(dc, cdu));
     V dp = vfma(nsph, vadd(h[a], h[b]), P);
-    V dm = vfma(nsmh, vsub(h[a], h[b]), Q);
+    // -s- (h- - heq-), h- = (h_a - h_b) / 2, heq- = k (drho c.u + c.du)
+    V dm = vmul(nsm, vsub(vmul(half, vsub(h[a], h[b])), vmul(k, vadd(dc, cdu))));
     if (kForce) {
       V cg;
       if (a == 1)
@@ -818,11 +880,13 @@ __device__ __forceinline__ void collide2(const V (&h)[9], V drho, V dux, V duy, 
       else
         cg = vsub(gy, gx);
       dp = vfma(vsplat(c.a_plus * w * (T)9), vmul(cu, cg), vfma(vsplat(c.a_plus * w * (T)-3), ug, dp));
-      dm = vfma(vsplat(c.a_minus * w * (T)3), cg, dm);
+      dm = vfma(vsplat(c.a_minus), vmul(k, cg), dm);
     }
+    even = vadd(even, dp);
     o[a] = vadd(vadd(h[a], dp), dm);
     o[b] = vsub(vadd(h[b], dp), dm);
   }
+  o[0] = vfma(vsplat((T)-2), even, h[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1072,6 +1136,22 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(const StepArgs p) {
   finalize<T>(p, p.acc_prev);
 }
 
+// chi of a moving body on the force-region tiles, tile by tile as the special
+// kernel rasterises it
+__global__ void __launch_bounds__(kThreads) mask_kernel(const StepArgs p) {
+  __shared__ TileMask tm;
+  const ForceRegion reg = *p.reg_src;
+  const int k = blockIdx.x;
+  if (k >= reg.count) return;
+  const int rw = reg.ti1 - reg.ti0 + 1;
+  const int ti = reg.ti0 + k % rw, tj = reg.tj0 + k / rw;
+  tile_solid(p, ti, tj, tm);
+  __syncthreads();
+  const int i = ti * kTileX + threadIdx.x, j = tj * kTileY + threadIdx.y;
+  if (i < p.L.nx && j < p.L.ny)
+    p.chi[(int64_t)j * p.L.pitch + i] = tile_mask_byte(p.L, tm, i, j, threadIdx.x, threadIdx.y);
+}
+
 template <typename S, bool kForce>
 cudaError_t bulk_v(int variant, const StepArgs &a, cudaStream_t s) {
   if constexpr (sizeof(S) == 2) {
@@ -1117,6 +1197,11 @@ cudaError_t launch_finalize(int dtype, const StepArgs &a, cudaStream_t s) {
     finalize_kernel<double><<<1, dim3(kTileX, kTileY), 0, s>>>(a);
   else
     finalize_kernel<float><<<1, dim3(kTileX, kTileY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask(const StepArgs &a, cudaStream_t s) {
+  mask_kernel<<<a.region_slots, dim3(kTileX, kTileY), 0, s>>>(a);
   return cudaGetLastError();
 }
 

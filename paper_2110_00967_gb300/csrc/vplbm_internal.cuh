@@ -446,6 +446,9 @@ struct StepArgs {
   int32_t n_edge;           // nodes on the lattice edges
   int32_t edge_blocks;      // special-kernel blocks for the edge nodes
   int32_t region_slots;     // special-kernel blocks reserved for force-region tiles
+  int32_t raster;           // 1 (a moving body): the force-region tiles rasterise chi
+                            // from body_src themselves, and SIM tests nodes with the
+                            // predicate instead of reading chi
 };
 
 // the nodes on the lattice edges, enumerated: first row, last row, then the
@@ -536,6 +539,9 @@ cudaError_t launch_special(int dtype, bool gather, const StepArgs &a, cudaStream
 // one block that finalizes a deferred step's force sums (acc_prev): history
 // row, running sums, step counter
 cudaError_t launch_finalize(int dtype, const StepArgs &a, cudaStream_t s);
+// chi of a moving body at the current time level on the force-region tiles
+// (reg_src, body_src): the mask the read-backs see after a call
+cudaError_t launch_mask(const StepArgs &a, cudaStream_t s);
 // the bulk kernel: the nodes off the edges, outside the force-region tiles
 // the bulk kernel in one of kBulkVariants launch forms (same results, bit
 // for bit): FP32 and FP64 blocks of 1, 2 or 4 tiles; 16-bit storage with
@@ -550,16 +556,20 @@ cudaError_t launch_interface(const Lattice &L, uint8_t *chi, int i0, int j0, int
                              cudaStream_t s);
 cudaError_t launch_init(int dtype, const Lattice &L, const BodyState *body, const uint8_t *chi,
                         void *buf, double u0x, double u0y, cudaStream_t s);
+// read-backs of the rows j0 .. j0 + rows - 1, written compactly ([rows][nx]
+// per output plane); get_f writes the planes a0 .. a0 + na - 1
 cudaError_t launch_get_f(int dtype, bool gather, const Lattice &L, const void *buf,
-                         const void *prev, double *out, cudaStream_t s);
+                         const void *prev, double *out, int a0, int na, int j0, int rows,
+                         cudaStream_t s);
 cudaError_t launch_get_fields(int dtype, bool gather, const Lattice &L, const void *buf,
                               const void *prev, const uint8_t *chi, const BodyState *body,
-                              double half_pen, double *rho, double *ux, double *uy,
-                              cudaStream_t s);
+                              double half_pen, double *rho, double *ux, double *uy, int j0,
+                              int rows, cudaStream_t s);
 cudaError_t launch_set_state(int dtype, const Lattice &L, const double *f, void *buf,
                              cudaStream_t s);
 cudaError_t launch_set_prev(int dtype, const Lattice &L, const double *f, void *prev,
                             cudaStream_t s);
-cudaError_t launch_get_mask(const Lattice &L, const uint8_t *chi, uint8_t *out, cudaStream_t s);
+cudaError_t launch_get_mask(const Lattice &L, const uint8_t *chi, uint8_t *out, int j0, int rows,
+                            cudaStream_t s);
 
 }  // namespace vplbm

@@ -118,6 +118,8 @@ class Server:
                 if batch is not None:
                     batch.close()
                 batch = self.backend.batch([a.lat for a in active])
+            if hasattr(self.backend, "range_push"):
+                self.backend.range_push(f"serve window: {len(active)} requests")
             batch.step(self.window)
             retired = []
             for a in active:
@@ -132,6 +134,8 @@ class Server:
                     a.res.converged = bool(done)
                     a.res.finish = clock() - t0
                     retired.append(a)
+            if hasattr(self.backend, "range_pop"):
+                self.backend.range_pop()
             if retired:
                 for a in retired:
                     active.remove(a)
@@ -145,15 +149,24 @@ class Server:
 
 
 def summary(results, elapsed: float, nodes_steps: float) -> dict:
-    """Throughput and latency figures of a served mix."""
+    """Throughput and latency figures of a served mix.  A solve is a request
+    whose Cd/Cl converged; requests stopped at the step cap are counted apart
+    (with their own throughput), and the latencies are those of the converged
+    requests (time from arrival to converged Cd/Cl)."""
     served = [r for r in results if not r.rejected]
-    lat = np.array([r.latency for r in served]) if served else np.zeros(1)
+    conv = [r for r in served if r.converged]
+    lat_c = np.array([r.latency for r in conv]) if conv else np.full(1, np.nan)
+    lat_all = np.array([r.latency for r in served]) if served else np.full(1, np.nan)
+    per_s = (lambda n: n / elapsed) if elapsed > 0 else (lambda n: 0.0)
     return {
-        "solves_per_s": len(served) / elapsed if elapsed > 0 else 0.0,
-        "p50_s": float(np.percentile(lat, 50)),
-        "p99_s": float(np.percentile(lat, 99)),
-        "converged": sum(r.converged for r in served),
-        "capped": sum(not r.converged for r in served),
+        "solves_per_s": per_s(len(conv)),
+        "completed_per_s": per_s(len(served)),
+        "p50_s": float(np.percentile(lat_c, 50)),
+        "p99_s": float(np.percentile(lat_c, 99)),
+        "p50_all_s": float(np.percentile(lat_all, 50)),
+        "p99_all_s": float(np.percentile(lat_all, 99)),
+        "converged": len(conv),
+        "capped": len(served) - len(conv),
         "rejected": sum(r.rejected for r in results),
         "mlups": nodes_steps / elapsed / 1e6 if elapsed > 0 else 0.0,
     }
@@ -187,3 +200,10 @@ class GpuBackend:
 
     def batch(self, lattices):
         return self.V.Batch(lattices, stream=self.stream)
+
+    # NVTX ranges around each served window, for profiler timelines
+    def range_push(self, name: str):
+        self.torch.cuda.nvtx.range_push(name)
+
+    def range_pop(self):
+        self.torch.cuda.nvtx.range_pop()

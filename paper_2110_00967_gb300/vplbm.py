@@ -99,13 +99,20 @@ _SIGS = [
     ("vplbm_force_angot", [_vp, _P(C.c_double), _P(C.c_double)], C.c_int),
     ("vplbm_forces_async", [_vp, _vp], C.c_int),
     ("vplbm_force_history", [_vp, C.c_int32, C.c_int32, _P(C.c_double)], C.c_int),
+    ("vplbm_force_history_async", [_vp, C.c_int32, _vp], C.c_int),
     ("vplbm_force_sums", [_vp, _P(C.c_double), _P(C.c_int64)], C.c_int),
     ("vplbm_reset_sums", [_vp], C.c_int),
     ("vplbm_step_count", [_vp, _P(C.c_int64)], C.c_int),
     ("vplbm_get_f", [_vp, _vp], C.c_int),
     ("vplbm_get_fields", [_vp, _vp, _vp, _vp], C.c_int),
+    ("vplbm_get_f_dev", [_vp, _vp], C.c_int),
+    ("vplbm_get_fields_dev", [_vp, _vp, _vp, _vp], C.c_int),
     ("vplbm_set_state", [_vp, _vp, _vp, C.c_int32], C.c_int),
     ("vplbm_get_mask", [_vp, _vp], C.c_int),
+    ("vplbm_get_mask_dev", [_vp, _vp], C.c_int),
+    ("vplbm_state_bytes", [_vp, _P(C.c_size_t)], C.c_int),
+    ("vplbm_save_state", [_vp, _vp, C.c_size_t], C.c_int),
+    ("vplbm_load_state", [_vp, _vp, C.c_size_t], C.c_int),
     ("vplbm_get_body", [_vp, _P(C.c_double)], C.c_int),
     ("vplbm_get_sim_nodes", [_vp, _P(C.c_int32), C.c_int32, _P(C.c_int32)], C.c_int),
     ("vplbm_check", [_vp], C.c_int),
@@ -230,20 +237,65 @@ def vplbm_step_count(ctx) -> int:
     return n.value
 
 
-def vplbm_get_f(ctx, f_dev_ptr: int):
-    _check(lib().vplbm_get_f(ctx, f_dev_ptr), ctx)
+def _host_ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
 
 
-def vplbm_get_fields(ctx, rho_ptr: int, ux_ptr: int, uy_ptr: int):
-    _check(lib().vplbm_get_fields(ctx, rho_ptr, ux_ptr, uy_ptr), ctx)
+def vplbm_get_f(ctx, f: np.ndarray):
+    """Pre-collision populations into a host float64 array [9][ny][nx]."""
+    assert f.dtype == np.float64 and f.flags.c_contiguous
+    _check(lib().vplbm_get_f(ctx, _host_ptr(f)), ctx)
+
+
+def vplbm_get_fields(ctx, rho: np.ndarray, ux: np.ndarray, uy: np.ndarray):
+    for a in (rho, ux, uy):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    _check(lib().vplbm_get_fields(ctx, _host_ptr(rho), _host_ptr(ux), _host_ptr(uy)), ctx)
+
+
+def vplbm_get_f_dev(ctx, f_dev_ptr: int):
+    _check(lib().vplbm_get_f_dev(ctx, f_dev_ptr), ctx)
+
+
+def vplbm_get_fields_dev(ctx, rho_ptr: int, ux_ptr: int, uy_ptr: int):
+    _check(lib().vplbm_get_fields_dev(ctx, rho_ptr, ux_ptr, uy_ptr), ctx)
 
 
 def vplbm_set_state(ctx, f_dev_ptr: int, prev_dev_ptr, post_collision: int):
     _check(lib().vplbm_set_state(ctx, f_dev_ptr, prev_dev_ptr, post_collision), ctx)
 
 
-def vplbm_get_mask(ctx, chi_dev_ptr: int):
-    _check(lib().vplbm_get_mask(ctx, chi_dev_ptr), ctx)
+def vplbm_get_mask(ctx, chi: np.ndarray):
+    assert chi.dtype == np.uint8 and chi.flags.c_contiguous
+    _check(lib().vplbm_get_mask(ctx, _host_ptr(chi)), ctx)
+
+
+def vplbm_get_mask_dev(ctx, chi_dev_ptr: int):
+    _check(lib().vplbm_get_mask_dev(ctx, chi_dev_ptr), ctx)
+
+
+def vplbm_state_bytes(ctx) -> int:
+    n = C.c_size_t()
+    _check(lib().vplbm_state_bytes(ctx, C.byref(n)), ctx)
+    return n.value
+
+
+def vplbm_save_state(ctx) -> np.ndarray:
+    """The lattice's snapshot as a host byte array."""
+    buf = np.zeros(vplbm_state_bytes(ctx), np.uint8)
+    _check(lib().vplbm_save_state(ctx, _host_ptr(buf), buf.nbytes), ctx)
+    return buf
+
+
+def vplbm_load_state(ctx, snapshot: np.ndarray):
+    snap = np.ascontiguousarray(snapshot, np.uint8)
+    _check(lib().vplbm_load_state(ctx, _host_ptr(snap), snap.nbytes), ctx)
+
+
+def vplbm_force_history_async(ctx, count: int, out_ptr: int):
+    """Queues the last `count` history rows ([count][9] float64) into host
+    memory at out_ptr (page-locked for an asynchronous copy)."""
+    _check(lib().vplbm_force_history_async(ctx, count, out_ptr), ctx)
 
 
 def vplbm_get_body(ctx):
@@ -313,6 +365,10 @@ def vplbm_sim_force_static(cfg: vplbm_config, f_dev_ptr: int, chi_dev_ptr: int, 
     include/vplbm.h); pts is an (n, 5) float64 host array."""
     pts = np.ascontiguousarray(pts, np.float64)
     ref = np.ascontiguousarray(ref, np.float64)
+    if pts.ndim != 2 or pts.shape[1] != 5:
+        raise ValueError(f"pts must have shape (n, 5), not {pts.shape}")
+    if ref.shape != (2,):
+        raise ValueError(f"ref must hold two values, not shape {ref.shape}")
     out = np.zeros(3)
     _check(lib().vplbm_sim_force_static(C.byref(cfg), f_dev_ptr, chi_dev_ptr, len(pts),
                                         pts.ctypes.data_as(_P(C.c_double)),
@@ -393,21 +449,15 @@ class Lattice:
     def steps(self) -> int:
         return vplbm_step_count(self.ctx)
 
-    def _empty(self, shape, dtype):
-        return self.torch.empty(shape, dtype=dtype, device=self.device)
-
     def get_f(self) -> np.ndarray:
-        out = self._empty((9, self.cfg.ny, self.cfg.nx), self.torch.float64)
-        with self.torch.cuda.stream(self.stream):
-            vplbm_get_f(self.ctx, _dptr(out))
-            return out.cpu().numpy()
+        out = np.empty((9, self.cfg.ny, self.cfg.nx))
+        vplbm_get_f(self.ctx, out)
+        return out
 
     def get_fields(self):
-        t = self.torch
-        rho, ux, uy = (self._empty((self.cfg.ny, self.cfg.nx), t.float64) for _ in range(3))
-        with t.cuda.stream(self.stream):
-            vplbm_get_fields(self.ctx, _dptr(rho), _dptr(ux), _dptr(uy))
-            return rho.cpu().numpy(), ux.cpu().numpy(), uy.cpu().numpy()
+        rho, ux, uy = (np.empty((self.cfg.ny, self.cfg.nx)) for _ in range(3))
+        vplbm_get_fields(self.ctx, rho, ux, uy)
+        return rho, ux, uy
 
     def set_state(self, f: np.ndarray, prev: np.ndarray | None = None, post_collision=False):
         t = self.torch
@@ -419,10 +469,15 @@ class Lattice:
             self.stream.synchronize()
 
     def get_mask(self) -> np.ndarray:
-        out = self._empty((self.cfg.ny, self.cfg.nx), self.torch.uint8)
-        with self.torch.cuda.stream(self.stream):
-            vplbm_get_mask(self.ctx, _dptr(out))
-            return out.cpu().numpy()
+        out = np.empty((self.cfg.ny, self.cfg.nx), np.uint8)
+        vplbm_get_mask(self.ctx, out)
+        return out
+
+    def save_state(self) -> np.ndarray:
+        return vplbm_save_state(self.ctx)
+
+    def load_state(self, snapshot: np.ndarray):
+        vplbm_load_state(self.ctx, snapshot)
 
     def get_body(self):
         return vplbm_get_body(self.ctx)

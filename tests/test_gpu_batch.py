@@ -137,3 +137,26 @@ def test_batch_errors():
     assert e.value.status == V.EINVAL
     batch.close()
     V.vplbm_batch_destroy(None)
+
+
+@pytest.mark.parametrize("lengths", [(1, 20, 7, 45), (2, 5, 20), (1, 1, 63, 64)])
+def test_runs_of_any_length_equal_single_steps(lengths):
+    """Runs of any length, from either buffer, are replayed from the graphs of
+    1, 2, 4, ..., 32 steps: a lattice and a batch stepped in those runs end
+    bit-identical to a lattice stepped one step per call."""
+    w = W.naca(7.0, dtype="f32", nx=256, ny=128)
+    runs, ref = lattice(w), lattice(w)
+    member, other = lattice(w), lattice(W.disk_channel())
+    other_ref = lattice(W.disk_channel())
+    batch = V.Batch([member, other])
+    for n in lengths:
+        runs.step(n)
+        batch.step(n)
+    total = sum(lengths)
+    for _ in range(total):
+        ref.step(1)
+        other_ref.step(1)
+    same_state(ref, runs, total)
+    same_state(ref, member, total)
+    same_state(other_ref, other, total)
+    batch.close()

@@ -5,7 +5,9 @@ relative for the FP64 path; 1e-5 relative on fields after 1000 FP32 steps
 (L-inf error over L-inf of the oracle field, for rho - 1, u_x, u_y); Cd/Cl
 within 1e-3 of the FP64 oracle.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -323,18 +325,20 @@ def test_sedimentation_full_size_first_1000_steps(case):
 # ---------------------------------------------------------------------------
 # FP32 and 16-bit storage against the FP64 oracle
 # ---------------------------------------------------------------------------
-def field_errors(lat, cfg, body, chi, f):
+def field_errors(lat, cfg, body, chi, f, fluid_only=False):
+    """L-inf errors of rho - 1, u_x, u_y over L-inf of the oracle's fields, on
+    every node or on the fluid nodes (chi = 0) only."""
     rho, ux, uy = lat.get_fields()
     r0, x0, y0 = o.fields(cfg, body, chi, f)
-    return rel_linf(rho - 1, r0 - 1), rel_linf(ux, x0), rel_linf(uy, y0)
+    sel = (chi == 0) if fluid_only else np.ones(chi.shape, bool)
+    return (rel_linf((rho - 1)[sel], (r0 - 1)[sel]), rel_linf(ux[sel], x0[sel]),
+            rel_linf(uy[sel], y0[sel]))
 
 
 FP32_CASES = {
-    # steady flows: the 1e-5 field bar of the FP32 path
     "disk-channel": lambda: W.disk_channel().with_(dtype="f32", steps=1000, u_ref=(0.05, 0.0)),
     "naca0-512": lambda: W.naca(0.0, dtype="f32", nx=512, ny=256, steps=1000),
-    # separated flow at 10 degrees: round-off differences grow with the shear
-    # layer, so fields are compared at 1e-3 and forces at the Cd/Cl bar
+    # separated flow at 10 degrees
     "naca10-512": lambda: W.naca(10.0, dtype="f32", nx=512, ny=256, steps=1000),
 }
 _ORACLE_RUNS = {}
@@ -354,23 +358,38 @@ def oracle_run(key):
 def test_fp32_after_1000_steps(key):
     """FP32 (offsets from the free-stream equilibrium) against the FP64 oracle
     after 1000 steps: field error (L-inf over L-inf of the oracle field,
-    rho - 1, u_x, u_y) <= 1e-5 on the steady airfoil flow; forces (MEM and
-    SIM) within 1e-3."""
+    rho - 1, u_x, u_y) <= 1e-5 on the fluid nodes of every case and on every
+    node of the airfoil cases; forces (MEM and SIM) within 1e-3.
+
+    The FP32 collision conserves mass and momentum exactly up to rounding
+    (the rest population as the remainder of the even changes, odd weights
+    with 2 k1 + 4 k2 = 1 in FP32); with the rounded weights every collision
+    was a source of 7.45e-9 s of the density and momentum offsets, which
+    compounded to 1e-5 in 1000 steps.  Inside the disk of the channel case the
+    penalization pins the velocity to the body's, so the density there has no
+    restoring flow: the rounding of its stored populations (offsets of about
+    0.017 from the free-stream equilibrium, an FP32 unit of 2e-9) moves mass
+    between solid nodes by the same small amounts step after step, and the
+    density inside the body drifts by about 1e-6 in 1000 steps (3.5e-5 of the
+    field's L-inf; the fluid nodes stay within 1.2e-6).  That node set is held
+    to 5e-5."""
     w = FP32_CASES[key]()
     lat = lattice(w)
     lat.step(w.steps)
     r = oracle_run(key)
     errs = field_errors(lat, r["cfg"], r["body"], r["chi"], r["f"])
-    print(key, "field errors", errs)
-    # the airfoil (the FP32 configuration) meets 1e-5; the confined disk
-    # channel (an FP64 configuration run here in FP32, BGK) reaches 2.3e-5 on
-    # rho - 1 and 1.6e-5 on u
-    bar = {"naca0-512": 1e-5, "naca10-512": 1e-3, "disk-channel": 3e-5}[key]
-    assert max(errs) <= bar, errs
+    fluid = field_errors(lat, r["cfg"], r["body"], r["chi"], r["f"], fluid_only=True)
+    print(key, "field errors, all nodes", errs, "fluid nodes", fluid)
+    assert max(fluid) <= 1e-5, fluid
+    assert max(errs) <= (5e-5 if key == "disk-channel" else 1e-5), errs
     fm, fs = lat.force_mem(), lat.force_sim()
     for g, ref in ((fm, r["mh"][-1]), (fs, r["sh"][-1])):
         scale = np.abs(ref[:2]).max()
         assert np.abs(g[:2] - ref[:2]).max() <= 1e-3 * scale, (g, ref)
+
+
+ENVELOPES = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                         "storage_envelopes.json")
 
 
 @pytest.mark.parametrize("offsets", ["free-stream", "weights"])
@@ -378,14 +397,20 @@ def test_fp32_after_1000_steps(key):
 @pytest.mark.parametrize("key", ["naca0-512", "naca10-512"])
 def test_16bit_storage_errors(dtype, key, offsets):
     """Offsets stored in FP16 / BF16 with an FP32 collide, either from the
-    free-stream equilibrium (u_ref = u_in) or from the lattice weights (f - w):
-    errors against the FP64 oracle after 1000 steps stay within bounds set by
-    the storage precision (2^-11 and 2^-8 relative on the offsets).  The
-    bounds are envelopes: about twice the largest error seen over two
-    orderings of the same FP32 collision arithmetic (one node per thread with
-    compiler-contracted FMAs, two nodes per thread in packed f32x2), since the
-    rounding of each stored value to 16 bits turns any change in the last bits
-    of the collision into a different trajectory."""
+    free-stream equilibrium (u_ref = u_in) or from the lattice weights (f - w),
+    against the FP64 oracle after 1000 steps.  The bound comes from the storage
+    format alone: tests/golden/storage_envelopes.json holds how far the FP64
+    oracle itself moves in 1000 steps when its stored offsets are rounded to
+    the format after every step.  The velocity error may reach three times
+    the oracle's own velocity error under that rounding, and each force error
+    three times the largest MEM or SIM force error of the two airfoil cases
+    with that format and those offsets (a force at one step is one sample of
+    the storage noise, and the library rounds a different sequence of values
+    than the emulation does)."""
+    cases = json.load(open(ENVELOPES))["cases"]
+    env = cases[f"{key}/{offsets}/{dtype}"]
+    forces = [cases[f"{c}/{offsets}/{dtype}"][e] for c in ("naca0-512", "naca10-512")
+              for e in ("force_mem", "force_sim")]
     u_ref = (0.05, 0.0) if offsets == "free-stream" else (0.0, 0.0)
     w = FP32_CASES[key]().with_(dtype=dtype, u_ref=u_ref)
     lat = lattice(w)
@@ -395,10 +420,10 @@ def test_16bit_storage_errors(dtype, key, offsets):
     fm, fs = lat.force_mem(), lat.force_sim()
     ferr = [np.abs(g[:2] - ref[:2]).max() / np.abs(ref[:2]).max()
             for g, ref in ((fm, r["mh"][-1]), (fs, r["sh"][-1]))]
-    print(dtype, key, offsets, "field errors", errs, "force errors", ferr)
-    bounds = {("f16", "free-stream"): (2e-3, 6e-3), ("f16", "weights"): (6e-3, 6e-3),
-              ("bf16", "free-stream"): (3e-2, 0.1), ("bf16", "weights"): (8e-2, 0.3)}
-    u_bound, f_bound = bounds[(dtype, offsets)]
+    u_bound = 3 * max(env["fields"][1:])
+    f_bound = 3 * max(forces)
+    print(dtype, key, offsets, "field errors", errs, "force errors", ferr,
+          "bounds", u_bound, f_bound)
     assert max(errs[1:]) <= u_bound and max(ferr) <= f_bound
 
 
@@ -601,3 +626,34 @@ def test_instability_is_latched():
         lat.check()
     assert e.value.status == V.EUNSTABLE
     lat.set_body(V.body_of(w.with_(u_in=(0.01, 0.0))))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("shape", [(300, 3), (131, 40), (2048, 1024)])
+def test_host_read_backs_equal_device_read_backs(dtype, shape):
+    """The host read-backs (staged a few rows at a time through the spare
+    population buffer) return exactly what the device read-backs write, on
+    lattices whose staging takes one chunk, several chunks, or (16-bit storage
+    on three rows) one population plane at a time; and stepping on afterwards
+    is unaffected by the staging."""
+    import torch
+    nx, ny = shape
+    w = small_case(("inlet", "outlet", "symmetry", "symmetry"), dtype=dtype, nx=nx, ny=ny,
+                   body="none" if ny < 12 else "disk")
+    a, b = lattice(w), lattice(w)
+    a.step(5)
+    b.step(5)
+    f = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+    fl = [torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
+    chi = torch.empty((ny, nx), dtype=torch.uint8, device="cuda")
+    V.vplbm_get_f_dev(a.ctx, f.data_ptr())
+    V.vplbm_get_fields_dev(a.ctx, *(t.data_ptr() for t in fl))
+    V.vplbm_get_mask_dev(a.ctx, chi.data_ptr())
+    torch.cuda.synchronize()
+    assert np.array_equal(a.get_f(), f.cpu().numpy())
+    for got, ref in zip(a.get_fields(), fl):
+        assert np.array_equal(got, ref.cpu().numpy())
+    assert np.array_equal(a.get_mask(), chi.cpu().numpy())
+    a.step(3)
+    b.step(3)
+    assert np.array_equal(a.get_f(), b.get_f())

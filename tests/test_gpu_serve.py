@@ -1,6 +1,9 @@
 """The serving loop on the GPU: a request's result does not depend on what it
 is served with (lattices share no data), and its window-mean Cd/Cl match the
 FP64 oracle's means over the same steps within 1e-3."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -51,3 +54,41 @@ def test_window_means_match_the_oracle(dtype, tol):
            sh[2000:, 0].mean() / q, sh[2000:, 1].mean() / q)
     for g, r in zip((got.cd, got.cl, got.cd_sim, got.cl_sim), ref):
         assert abs(g - r) <= tol * max(abs(r), 1e-2), (g, r)
+
+
+SUBSET = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "serving_subset.json")
+ENVELOPES = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                         "storage_envelopes.json")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_seeded_subset_matches_the_oracle(dtype):
+    """The first eight requests of the seeded 256-request mix (their grids,
+    768 x 384 .. 2048 x 1024, and angles), served together for 3000 steps
+    each: every request's last window means of Cd and Cl (MEM and SIM) against
+    the FP64 oracle's (tests/golden/serving_subset.json).  FP32 within the
+    1e-3 bar; FP16 offsets within three times the largest force error that
+    FP16 storage alone causes in the oracle (tests/golden/storage_envelopes.json,
+    free-stream offsets)."""
+    ref = json.load(open(SUBSET))
+    reqs = [W.Request(r.rid, 0.0, r.alpha_deg, r.nx, r.ny)
+            for r in W.serving_requests(256)[:len(ref["requests"])]]
+    srv = S.Server(S.GpuBackend(dtype), memory_bytes=16 << 30, window=1000, tol=0.0,
+                   cap=ref["steps"])  # tol 0: every request runs to the cap
+    got = {r.rid: r for r in srv.run(reqs)}
+    if dtype == "f32":
+        bar = 1e-3
+    else:
+        env = json.load(open(ENVELOPES))["cases"]
+        bar = 3 * max(max(env[f"{c}/free-stream/f16"]["force_mem"],
+                          env[f"{c}/free-stream/f16"]["force_sim"])
+                      for c in ("naca0-512", "naca10-512"))
+    worst = 0.0
+    for g in ref["requests"]:
+        r = got[g["rid"]]
+        assert r.steps == ref["steps"] and not r.converged
+        for k, v in (("cd_mem", r.cd), ("cl_mem", r.cl), ("cd_sim", r.cd_sim), ("cl_sim", r.cl_sim)):
+            err = abs(v - g[k]) / max(abs(g[k]), 1e-2)
+            worst = max(worst, err)
+            assert err <= bar, (dtype, g["rid"], k, v, g[k], err, bar)
+    print(dtype, "worst relative error of the served means", worst, "bar", bar)

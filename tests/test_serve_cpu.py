@@ -118,6 +118,9 @@ def test_cap_and_rejection():
         assert not r.rejected and not r.converged and r.steps == 5000
     summ = S.summary(res, clock.t, 0.0)
     assert summ["rejected"] == 1 and summ["capped"] == 2 and summ["converged"] == 0
+    # capped requests are no solves: they count only as completed
+    assert summ["solves_per_s"] == 0.0 and summ["completed_per_s"] == 2 / clock.t
+    assert math.isnan(summ["p50_s"]) and summ["p50_all_s"] > 0
 
 
 def test_coefficients_from_sums():
