@@ -240,6 +240,9 @@ def run_ours(args, rank, world, local_rank):
     # the bulk kernel's launch form, timed with the five lattices side by side,
     # before the warm-up
     variants = [batch.autotune(64)]
+    # the step graphs of a run of args.steps steps, captured before the timed
+    # region (one graph per lattice for up to 32 steps)
+    batch.prepare(args.steps)
     batch.step(args.warmup)
     torch.cuda.synchronize()
 

@@ -162,8 +162,25 @@ vplbm_status vplbm_set_body(vplbm_ctx *ctx, const vplbm_body *body);
  * conditions (Eq. eqBd, Sec. 3.1); the MEM force of Eq. MMEL / Eq. fluidtorque
  * on the post-collision populations; the SIM force of Eq. defFf on the
  * pre-collision populations (when due); and, for a moving body, the FP64
- * rigid-body update of Eqs. dep1 / theta2 followed by re-rasterising chi. */
+ * rigid-body update of Eqs. dep1 / theta2 followed by re-rasterising chi.
+ * Runs of steps are replayed from CUDA graphs of 1, 2, 4, ..., 32 steps,
+ * captured (all of them, from either population buffer) at the first run
+ * that can use one: when the lattice is past its first step and SIM runs
+ * every step or never.  The call returns with the last step's forces in the
+ * history. */
 vplbm_status vplbm_step(vplbm_ctx *ctx, int32_t nsteps);
+
+/* Captures and uploads, now, the step graphs that runs of nsteps steps use
+ * (a run of more than 32 steps is replayed in 32-step graphs and one graph of
+ * the remainder), so that the first run of that length pays for no capture
+ * and replays one graph where it would otherwise replay several (20 steps:
+ * one graph instead of 16 + 4).  No counterpart in the paper; it changes no
+ * result.  The prepared length is kept until the context is destroyed (graphs
+ * dropped by vplbm_set_body or a change of launch form are captured again at
+ * the next run).  Synchronises the stream.  ESTATE before vplbm_set_body.
+ * Lattices whose SIM runs on some steps only (sim_every > 1) queue their
+ * steps one by one; the call does nothing for them. */
+vplbm_status vplbm_prepare(vplbm_ctx *ctx, int32_t nsteps);
 
 /* Force (F[0], F[1]) and torque (*T) of the last step from MEM (Eq. MMEL,
  * Eq. fluidtorque), host outputs.  Synchronises the stream.  ESTATE before the
@@ -295,7 +312,8 @@ vplbm_status vplbm_launch_count(vplbm_ctx *ctx, int64_t *n);
  * from the edges and the body comes in three launch forms which compute the
  * same values bit for bit: FP32/FP64 storage, blocks of one, two or four
  * 128 x 2 tiles; 16-bit storage, eight nodes per thread at 96 or 126
- * registers, or four nodes per thread.  Form 0 is the default.
+ * registers, or four nodes per thread.
+ * Form 0 is the default.
  *
  * vplbm_autotune times the forms on this lattice's own steps: three passes
  * over the forms, each form running 32 untimed steps (its step graph is
@@ -321,14 +339,13 @@ vplbm_status vplbm_bulk_variant(vplbm_ctx *ctx, int32_t *variant);
  * of every vplbm_batch_step: steps of different lattices overlap, and one
  * lattice's latency-bound work (force reductions, a moving body's update) runs
  * while others use the memory bandwidth.  Each lattice ends in the state, with
- * the force histories and sums, that stepping it alone would give.  Runs of
- * 32 steps in which every lattice starts from an even time level since its
- * last pre-collision state (vplbm_set_body or vplbm_set_state) and evaluates
- * SIM every step or never are replayed from one CUDA graph holding all n
- * lattices' steps: one host launch per 32 n lattice steps.  The rest are
- * queued step by step.  The parameter studies of Sec. 4 (one lattice per
- * angle of attack, per estimator, per resolution) are such batches; the paper
- * itself steps one lattice at a time. */
+ * the force histories and sums, that stepping it alone would give.  Each
+ * lattice's steps are replayed from its own step graphs (runs of 1, 2, 4, ...,
+ * 32 steps, as vplbm_step replays them) where they apply, and the lattices
+ * meet only at the end of the call, so that none waits for another between
+ * runs.  The parameter studies of Sec. 4 (one lattice per angle of attack, per
+ * estimator, per resolution) are such batches; the paper itself steps one
+ * lattice at a time. */
 typedef struct vplbm_batch vplbm_batch;
 
 /* ctxs: host array of n >= 1 distinct contexts created on the current device.
@@ -346,6 +363,11 @@ vplbm_status vplbm_batch_create(vplbm_ctx *const *ctxs, int32_t n, void *cuda_st
  * (nothing is queued then).  A vplbm_set_body on a member between calls is
  * seen by the next call. */
 vplbm_status vplbm_batch_step(vplbm_batch *batch, int32_t nsteps);
+
+/* vplbm_prepare for every lattice of the batch (the runs of a batch call are
+ * at most 32 steps per lattice; each graph is uploaded on its lattice's chain
+ * stream).  ESTATE when a lattice has no body placed. */
+vplbm_status vplbm_batch_prepare(vplbm_batch *batch, int32_t nsteps);
 
 /* The bulk kernel's launch form for every lattice of the batch, timed on the
  * batch's own steps as vplbm_autotune does for one lattice (the same form on

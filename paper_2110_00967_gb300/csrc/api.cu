@@ -27,11 +27,11 @@ struct Range {
 };
 
 constexpr size_t kAlign = 256;
-// Runs of steps are replayed from CUDA graphs of 1, 2, 4, ..., 32 steps, one
-// per length and per starting buffer: any step count is a sum of at most
-// kGraphLevels graph launches per 63 steps.
-constexpr int kGraphLevels = 6;
-constexpr int kGraphMax = 1 << (kGraphLevels - 1);  // 32 steps
+// Runs of steps are replayed from CUDA graphs of up to kGraphMax steps, one
+// per length and per starting buffer: always 1, 2, 4, ..., 32 steps (any
+// step count is then a sum of at most six launches per 63 steps), and any
+// other length a caller prepares (vplbm_prepare) for runs of that length.
+constexpr int kGraphMax = 32;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -248,8 +248,9 @@ struct vplbm_ctx {
   long long steps = 0;
   int64_t launches = 0;
   uint64_t generation = 0;  // bumped whenever captured step graphs go stale
-  // graphs[p][k]: 2^k steps starting from buffer p, ending with finalized forces
-  cudaGraphExec_t graphs[2][kGraphLevels] = {};
+  // graphs[p][n]: n steps starting from buffer p, ending with finalized forces
+  cudaGraphExec_t graphs[2][kGraphMax + 1] = {};
+  bool graph_wanted[kGraphMax + 1] = {};  // lengths beyond the powers of two
   bool graphs_ready = false;
   cudaStream_t side = nullptr;      // the special kernel's stream
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -416,33 +417,40 @@ void drop_graphs(vplbm_ctx *c) {
   c->graphs_ready = false;
 }
 
-// the longest graph that fits in `left` steps: its level k (2^k steps)
-int graph_level(int left) {
-  int k = 0;
-  while (k + 1 < kGraphLevels && (2 << k) <= left) ++k;
-  return k;
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// the longest captured graph that fits in `left` steps
+int graph_length(const vplbm_ctx *c, int left) {
+  for (int n = std::min(left, kGraphMax); n > 1; --n)
+    if (c->graphs[c->cur][n]) return n;
+  return 1;
 }
 
-// Captures the step graphs of every length and both starting buffers (valid
-// when SIM runs every step or never: the step kernels are then the same for
-// every step).  Each graph begins with no force sums pending and ends with
-// its last step's sums finalized.  All are captured together, at the first
-// run that needs one, so that later runs of any length find theirs.
-vplbm_status ensure_graphs(vplbm_ctx *c) {
+// Captures the step graphs of every wanted length (the powers of two up to
+// kGraphMax and the prepared lengths) and both starting buffers that are not
+// captured yet (valid when SIM runs every step or never: the step kernels are
+// then the same for every step).  Each graph begins with no force sums
+// pending and ends with its last step's sums finalized (and a moving body's
+// mask refreshed).  They are captured together, at the first run that needs
+// one, so that later runs of any length find theirs; each is uploaded on the
+// stream s that will launch it.
+vplbm_status ensure_graphs(vplbm_ctx *c, cudaStream_t s) {
   if (c->graphs_ready) return VPLBM_OK;
   if (!c->capture_stream)
     VPLBM_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
   const int64_t launches = c->launches;
   const bool stale = c->mask_stale;
   const bool do_sim = c->sim_every == 1 && c->n_sim > 0;
-  for (int p = 0; p < 2; ++p)
-    for (int k = 0; k < kGraphLevels; ++k) {
+  for (int n = 1; n <= kGraphMax; ++n) {
+    if (!is_pow2(n) && !c->graph_wanted[n]) continue;
+    for (int p = 0; p < 2; ++p) {
+      if (c->graphs[p][n]) continue;
       cudaGraph_t g = nullptr;
       VPLBM_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t e = cudaSuccess;
       const int cur = c->cur;
-      c->cur = (p + (1 << k)) & 1;  // the mask refresh reads the level the graph ends at
-      for (int q = 0; q < (1 << k) && e == cudaSuccess; ++q)
+      c->cur = (p + n) & 1;  // the level the graph ends at, for the end-of-run work
+      for (int q = 0; q < n && e == cudaSuccess; ++q)
         e = queue_step(c, c->capture_stream, (p + q) & 1, false, do_sim);
       if (e == cudaSuccess) e = flush_forces(c, c->capture_stream);
       if (e == cudaSuccess) e = refresh_mask(c, c->capture_stream);
@@ -459,21 +467,50 @@ vplbm_status ensure_graphs(vplbm_ctx *c) {
         drop_graphs(c);
         return cuda_fail(c, e2, "cudaStreamEndCapture");
       }
-      e = cudaGraphInstantiate(&c->graphs[p][k], g, 0);
+      e = cudaGraphInstantiate(&c->graphs[p][n], g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) {
-        c->graphs[p][k] = nullptr;
+        c->graphs[p][n] = nullptr;
         drop_graphs(c);
         return cuda_fail(c, e, "cudaGraphInstantiate");
       }
-      // uploaded now, so that the first launch of each does not pay for it
-      e = cudaGraphUpload(c->graphs[p][k], c->stream);
+      e = cudaGraphUpload(c->graphs[p][n], s);  // so that its first launch does not pay for it
       if (e != cudaSuccess) {
         drop_graphs(c);
         return cuda_fail(c, e, "cudaGraphUpload");
       }
     }
+  }
   c->graphs_ready = true;
+  return VPLBM_OK;
+}
+
+// Queues nsteps steps of one lattice on stream s: each run from the longest
+// step graph that fits (when the lattice is past its first step and SIM runs
+// every step or never), single steps otherwise; ends with the forces
+// finalized and a moving body's mask refreshed.
+vplbm_status run_steps(vplbm_ctx *c, cudaStream_t s, int nsteps) {
+  int left = nsteps;
+  const bool graphable = c->sim_every <= 1;
+  while (left > 0) {
+    if (graphable && !c->pre) {
+      VPLBM_CUDA(c, flush_forces(c, s));  // a graph starts with nothing pending
+      if (vplbm_status st = ensure_graphs(c, s)) return st;
+      const int n = graph_length(c, left);
+      VPLBM_CUDA(c, cudaGraphLaunch(c->graphs[c->cur][n], s));
+      c->launches += 2 * n + 1 + (c->body_host.moving ? 1 : 0);
+      c->steps += n;
+      c->cur ^= n & 1;
+      c->pending = false;
+      c->mask_stale = false;  // the graph ends with the mask refreshed
+      left -= n;
+      continue;
+    }
+    if (vplbm_status st = one_step(c, s)) return st;
+    --left;
+  }
+  VPLBM_CUDA(c, flush_forces(c, s));  // every call returns with its forces finalized
+  VPLBM_CUDA(c, refresh_mask(c, s));  // and with the mask of the current level
   return VPLBM_OK;
 }
 
@@ -793,30 +830,36 @@ vplbm_status vplbm_step(vplbm_ctx *c, int32_t nsteps) {
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (nsteps < 0) return fail(c, VPLBM_EINVAL, "nsteps must be >= 0");
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "no body placed (vplbm_set_body)");
-  cudaStream_t s = c->stream;
-  int left = nsteps;
-  const bool graphable = c->sim_every <= 1;
-  while (left > 0) {
-    if (graphable && !c->pre) {
-      // the longest captured run that fits, from the current buffer
-      VPLBM_CUDA(c, flush_forces(c, s));  // a graph starts with nothing pending
-      if (vplbm_status st = ensure_graphs(c)) return st;
-      const int k = graph_level(left), n = 1 << k;
-      VPLBM_CUDA(c, cudaGraphLaunch(c->graphs[c->cur][k], s));
-      c->launches += 2 * n + 1 + (c->body_host.moving ? 1 : 0);
-      c->steps += n;
-      c->cur ^= n & 1;
-      c->pending = false;
-      c->mask_stale = false;  // the graph ends with the mask refreshed
-      left -= n;
-      continue;
-    }
-    if (vplbm_status st = one_step(c, s)) return st;
-    --left;
-  }
-  VPLBM_CUDA(c, flush_forces(c, s));  // every call returns with its forces finalized
-  VPLBM_CUDA(c, refresh_mask(c, s));  // and with the mask of the current level
-  return VPLBM_OK;
+  return run_steps(c, c->stream, nsteps);
+}
+
+}  // extern "C"
+
+namespace {
+
+// marks the graph length a run of nsteps steps ends with (beyond the full
+// kGraphMax runs) for capture; true when a new length was marked
+bool want_length(vplbm_ctx *c, int nsteps) {
+  const int r = nsteps > kGraphMax ? nsteps % kGraphMax : nsteps;
+  if (r <= 1 || is_pow2(r) || c->graph_wanted[r]) return false;
+  c->graph_wanted[r] = true;
+  c->graphs_ready = false;  // ensure_graphs captures the missing lengths only
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+vplbm_status vplbm_prepare(vplbm_ctx *c, int32_t nsteps) {
+  Range range_("vplbm_prepare");
+  if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return fail(c, VPLBM_EINVAL, "nsteps must be >= 0");
+  if (!c->has_body) return fail(c, VPLBM_ESTATE, "no body placed (vplbm_set_body)");
+  want_length(c, nsteps);
+  if (c->sim_every > 1) return VPLBM_OK;  // steps are queued one by one
+  if (vplbm_status st = ensure_graphs(c, c->stream)) return st;
+  return sync(c);
 }
 
 // one history row: MEM (F_x, F_y, T), SIM (same), volume integral (same)
@@ -1317,17 +1360,12 @@ const char *vplbm_last_error(const vplbm_ctx *c) { return c ? c->err.c_str() : g
 
 struct vplbm_batch {
   std::vector<vplbm_ctx *> ctxs;
-  std::vector<uint64_t> generations;  // of the contexts when the graph was captured
   cudaStream_t stream = nullptr;
-  cudaStream_t capture_stream = nullptr;
-  // graphs[p][k]: 2^k steps of every lattice, each starting from buffer p
-  cudaGraphExec_t graphs[2][kGraphLevels] = {};
-  bool graphs_ready = false;
   std::vector<cudaEvent_t> ev_in;   // each lattice's stream -> the batch stream
   cudaEvent_t ev_out = nullptr;     // the batch stream -> each lattice's stream
   std::vector<cudaStream_t> chain;  // one stream per lattice: the lattices' steps run side by side
-  std::vector<cudaEvent_t> ev_chain;  // end of each chain -> the batch (or capture) stream
-  cudaEvent_t ev_fork = nullptr;      // start of a call on the batch (or capture) stream
+  std::vector<cudaEvent_t> ev_chain;  // end of each chain -> the batch stream
+  cudaEvent_t ev_fork = nullptr;      // start of a call on the batch stream
 };
 
 namespace {
@@ -1344,16 +1382,6 @@ vplbm_status batch_cuda(cudaError_t e, const char *where) {
 // a failure of a per-lattice call, reported through the global text
 vplbm_status batch_ctx_fail(vplbm_status st, int k, const vplbm_ctx *c) {
   return batch_fail(st, fmt("lattice %d: %s", k, c->err.c_str()));
-}
-
-void batch_drop_graph(vplbm_batch *b) {
-  for (auto &row : b->graphs)
-    for (cudaGraphExec_t &g : row)
-      if (g) {
-        cudaGraphExecDestroy(g);
-        g = nullptr;
-      }
-  b->graphs_ready = false;
 }
 
 // The lattices share no data, so each runs its steps on a stream of its own
@@ -1374,101 +1402,6 @@ cudaError_t batch_join(vplbm_batch *b, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_chain[q], 0);
   }
   return e;
-}
-
-// Finalizes the lattices' pending force sums and refreshes the masks of
-// moving bodies, each lattice on its chain.
-cudaError_t batch_flush(vplbm_batch *b, cudaStream_t s) {
-  bool any = false;
-  for (vplbm_ctx *c : b->ctxs) any = any || c->pending || c->mask_stale;
-  if (!any) return cudaSuccess;
-  cudaError_t e = batch_fork(b, s);
-  for (size_t q = 0; q < b->ctxs.size() && e == cudaSuccess; ++q) {
-    e = flush_forces(b->ctxs[q], b->chain[q]);
-    if (e == cudaSuccess) e = refresh_mask(b->ctxs[q], b->chain[q]);
-  }
-  if (e == cudaSuccess) e = batch_join(b, s);
-  return e;
-}
-
-// The batch's step graphs, as ensure_graphs captures them for one lattice:
-// 2^k steps of every lattice, each lattice on its chain, every lattice
-// starting from buffer p, for every length and both p.
-vplbm_status batch_capture(vplbm_batch *b) {
-  batch_drop_graph(b);
-  if (!b->capture_stream) {
-    cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return batch_cuda(e, "cudaStreamCreateWithFlags");
-  }
-  std::vector<int64_t> launches;
-  for (vplbm_ctx *c : b->ctxs) launches.push_back(c->launches);
-  for (int p = 0; p < 2; ++p)
-    for (int k = 0; k < kGraphLevels; ++k) {
-      cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
-      if (e != cudaSuccess) {
-        batch_drop_graph(b);
-        return batch_cuda(e, "cudaStreamBeginCapture");
-      }
-      e = batch_fork(b, b->capture_stream);
-      std::vector<int> cur;
-      std::vector<char> stale;
-      for (vplbm_ctx *c : b->ctxs) {
-        cur.push_back(c->cur);
-        stale.push_back(c->mask_stale ? 1 : 0);
-        c->cur = (p + (1 << k)) & 1;  // the level the graph ends at, for the end of run work
-      }
-      for (int q = 0; q < (1 << k) && e == cudaSuccess; ++q)
-        for (size_t m = 0; m < b->ctxs.size() && e == cudaSuccess; ++m) {
-          vplbm_ctx *c = b->ctxs[m];
-          e = queue_step(c, b->chain[m], (p + q) & 1, false, c->sim_every == 1 && c->n_sim > 0);
-        }
-      // the graph ends with the forces finalized and the masks refreshed
-      for (size_t m = 0; m < b->ctxs.size() && e == cudaSuccess; ++m) {
-        e = flush_forces(b->ctxs[m], b->chain[m]);
-        if (e == cudaSuccess) e = refresh_mask(b->ctxs[m], b->chain[m]);
-      }
-      if (e == cudaSuccess) e = batch_join(b, b->capture_stream);
-      for (size_t m = 0; m < b->ctxs.size(); ++m) {
-        b->ctxs[m]->launches = launches[m];
-        b->ctxs[m]->cur = cur[m];
-        b->ctxs[m]->mask_stale = stale[m] != 0;
-      }
-      cudaGraph_t g = nullptr;
-      const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
-      if (e != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        batch_drop_graph(b);
-        return batch_cuda(e, "capture of a batch graph");
-      }
-      if (e2 != cudaSuccess) {
-        batch_drop_graph(b);
-        return batch_cuda(e2, "cudaStreamEndCapture");
-      }
-      e = cudaGraphInstantiate(&b->graphs[p][k], g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) {
-        b->graphs[p][k] = nullptr;
-        batch_drop_graph(b);
-        return batch_cuda(e, "cudaGraphInstantiate");
-      }
-      // uploaded now, so that the first launch of each does not pay for it
-      e = cudaGraphUpload(b->graphs[p][k], b->stream);
-      if (e != cudaSuccess) {
-        batch_drop_graph(b);
-        return batch_cuda(e, "cudaGraphUpload");
-      }
-    }
-  b->graphs_ready = true;
-  b->generations.clear();
-  for (vplbm_ctx *c : b->ctxs) b->generations.push_back(c->generation);
-  return VPLBM_OK;
-}
-
-bool batch_graph_current(const vplbm_batch *b) {
-  if (!b->graphs_ready) return false;
-  for (size_t q = 0; q < b->ctxs.size(); ++q)
-    if (b->ctxs[q]->generation != b->generations[q]) return false;
-  return true;
 }
 
 }  // namespace
@@ -1539,6 +1472,25 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int32_t trials, int32_t *varia
   return VPLBM_OK;
 }
 
+vplbm_status vplbm_batch_prepare(vplbm_batch *b, int32_t nsteps) {
+  Range range_("vplbm_batch_prepare");
+  if (!b) return batch_fail(VPLBM_EINVAL, "vplbm_batch_prepare: batch is NULL");
+  if (nsteps < 0) return batch_fail(VPLBM_EINVAL, "vplbm_batch_prepare: nsteps must be >= 0");
+  for (size_t k = 0; k < b->ctxs.size(); ++k) {
+    vplbm_ctx *c = b->ctxs[k];
+    if (!c->has_body)
+      return batch_fail(VPLBM_ESTATE, fmt("vplbm_batch_prepare: lattice %zu has no body placed", k));
+    // the runs of a batch call are at most kGraphMax steps per lattice
+    want_length(c, nsteps);
+    if (c->sim_every > 1) continue;
+    if (vplbm_status st = ensure_graphs(c, b->chain[k])) return batch_ctx_fail(st, (int)k, c);
+  }
+  for (cudaStream_t st : b->chain)
+    if (const cudaError_t e = cudaStreamSynchronize(st); e != cudaSuccess)
+      return batch_cuda(e, "vplbm_batch_prepare: cudaStreamSynchronize");
+  return VPLBM_OK;
+}
+
 vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
   Range range_("vplbm_batch_step");
   if (!b) return batch_fail(VPLBM_EINVAL, "vplbm_batch_step: batch is NULL");
@@ -1557,43 +1509,20 @@ vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_in[k], 0);
     if (e != cudaSuccess) return batch_cuda(e, "vplbm_batch_step: ordering after a lattice stream");
   }
-  bool graphable = true;
-  for (vplbm_ctx *c : b->ctxs) graphable = graphable && c->sim_every <= 1;
-  int left = nsteps;
-  while (left > 0) {
-    // graphs need every lattice past its first step and all at one parity
-    bool aligned = graphable;
-    for (vplbm_ctx *c : b->ctxs) aligned = aligned && !c->pre && c->cur == b->ctxs[0]->cur;
-    if (aligned) {
-      // a graph starts with no lattice's force sums pending
-      if (const cudaError_t e = batch_flush(b, s); e != cudaSuccess)
-        return batch_cuda(e, "vplbm_batch_step: finalizing force sums");
-      if (!batch_graph_current(b))
-        if (vplbm_status st = batch_capture(b)) return st;
-      const int k = graph_level(left), len = 1 << k;
-      const cudaError_t e = cudaGraphLaunch(b->graphs[b->ctxs[0]->cur][k], s);
-      if (e != cudaSuccess) return batch_cuda(e, "vplbm_batch_step: cudaGraphLaunch");
-      for (vplbm_ctx *c : b->ctxs) {
-        c->launches += 2 * len + 1 + (c->body_host.moving ? 1 : 0);
-        c->steps += len;
-        c->cur ^= len & 1;
-        c->pending = false;
-        c->mask_stale = false;
-      }
-      left -= len;
-      continue;
-    }
-    if (const cudaError_t e = batch_fork(b, s); e != cudaSuccess)
-      return batch_cuda(e, "vplbm_batch_step: forking the lattice chains");
+  // each lattice runs its own steps (its step graphs where they apply) on its
+  // chain, forked from s and joined back; the chains meet only at the end of
+  // the call, so no lattice waits for another between runs of steps.  The
+  // calls are issued in rounds of at most 32 steps per lattice, so that the
+  // lattices' work is interleaved on the host too.
+  if (const cudaError_t e = batch_fork(b, s); e != cudaSuccess)
+    return batch_cuda(e, "vplbm_batch_step: forking the lattice chains");
+  for (int left = nsteps; left > 0; left -= std::min(left, kGraphMax)) {
+    const int run = std::min(left, kGraphMax);
     for (int k = 0; k < n; ++k)
-      if (vplbm_status st = one_step(b->ctxs[k], b->chain[k])) return batch_ctx_fail(st, k, b->ctxs[k]);
-    if (const cudaError_t e = batch_join(b, s); e != cudaSuccess)
-      return batch_cuda(e, "vplbm_batch_step: joining the lattice chains");
-    --left;
+      if (vplbm_status st = run_steps(b->ctxs[k], b->chain[k], run)) return batch_ctx_fail(st, k, b->ctxs[k]);
   }
-  // every call returns with its forces finalized
-  if (const cudaError_t e = batch_flush(b, s); e != cudaSuccess)
-    return batch_cuda(e, "vplbm_batch_step: finalizing force sums");
+  if (const cudaError_t e = batch_join(b, s); e != cudaSuccess)
+    return batch_cuda(e, "vplbm_batch_step: joining the lattice chains");
   // and each lattice's own stream follows the batch's work
   cudaError_t e = cudaEventRecord(b->ev_out, s);
   for (int k = 0; k < n && e == cudaSuccess; ++k)
@@ -1604,8 +1533,6 @@ vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
 
 void vplbm_batch_destroy(vplbm_batch *b) {
   if (!b) return;
-  batch_drop_graph(b);
-  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   for (cudaEvent_t ev : b->ev_in)
     if (ev) cudaEventDestroy(ev);
   if (b->ev_out) cudaEventDestroy(b->ev_out);

@@ -519,16 +519,191 @@ __device__ __forceinline__ void collide(const T (&h)[9], T drho, T dux, T duy, T
   o[0] = h[0] - (T)2 * even;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 arithmetic of the 16-bit forms' fluid-node update in the packed f32x2
+// instructions of sm_100 and later (one instruction for two nodes).  The
+// special kernel updates its 16-bit fluid nodes with the same instructions,
+// the node in both lanes: the compiler fuses some packed multiplies with a
+// following add (even when the PTX names a rounding mode), so only the same
+// instruction sequence gives a node the same bits in either kernel.
+// ---------------------------------------------------------------------------
+struct F2 {
+  float2 v;
+};
+__device__ __forceinline__ unsigned long long f2_bits(F2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.v.x), "f"(a.v.y));
+  return r;
+}
+__device__ __forceinline__ F2 bits_f2(unsigned long long r) {
+  F2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.v.x), "=f"(a.v.y) : "l"(r));
+  return a;
+}
+template <typename V>
+__device__ __forceinline__ V vsplat(float c);
+template <>
+__device__ __forceinline__ F2 vsplat<F2>(float c) { return F2{make_float2(c, c)}; }
+__device__ __forceinline__ F2 vpair(float x, float y) { return F2{make_float2(x, y)}; }
+__device__ __forceinline__ F2 vsame(float x) { return F2{make_float2(x, x)}; }
+__device__ __forceinline__ F2 vadd(F2 a, F2 b) { return F2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 vmul(F2 a, F2 b) { return F2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return F2{__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2 vsub(F2 a, F2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(r);
+}
+__device__ __forceinline__ F2 vrcp(F2 a) { return vpair(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
+__device__ __forceinline__ float vlo(F2 a) { return a.v.x; }
+__device__ __forceinline__ float vhi(F2 a) { return a.v.y; }
+__device__ __forceinline__ bool rho_bad(float r) { return !(r > 0.f) || !isfinite(r); }
+
+// The collision of collide() in the packed FP32 arithmetic above, with the
+// relaxation rate and weights folded into the even part's coefficients: for
+// each pair
+// (a, opp(a))
+//   s+ heq+ = s+ w K + 4.5 s+ w X,  X = drho (c.u)^2 + (c.du)(c.u + c.u_ref),
+//   K = drho (1 - 1.5 |u|^2) - 1.5 (|u|^2 - |u_ref|^2),
+// the same terms as heq_a = w_a [drho (1 + Q_a(u)) + Q_a(u) - Q_a(u_ref)].  The
+// odd part keeps collide()'s form -s- (h- - k (drho c.u + c.du)) with the
+// coefficients k of odd_w (its momentum is then exact: a folded s- k would
+// round differently from s-), and the rest population takes the even
+// changes' remainder as in collide().
+template <typename V, typename T, bool kForce>
+__device__ __forceinline__ void collide2(const V (&h)[9], V drho, V dux, V duy, V gx, V gy,
+                                         const Consts<T> &c, V (&o)[9]) {
+  const V urx = vsplat<V>(c.urx), ury = vsplat<V>(c.ury);
+  const V ux = vadd(urx, dux), uy = vadd(ury, duy);
+  const V uu = vfma(ux, ux, vmul(uy, uy));
+  const V dsu = vfma(dux, vadd(ux, urx), vmul(duy, vadd(uy, ury)));
+  const V m15 = vsplat<V>((T)-1.5);
+  const V K = vfma(m15, dsu, vmul(drho, vfma(m15, uu, vsplat<V>((T)1))));
+  V ug{};
+  if (kForce) ug = vfma(ux, gx, vmul(uy, gy));
+  const V nsph = vsplat<V>((T)-0.5 * c.s_plus), nsm = vsplat<V>(-c.s_minus), half = vsplat<V>((T)0.5);
+  V even = vsplat<V>((T)0);
+#pragma unroll
+  for (int a = 1; a <= 6; ++a) {
+    if (a == 3 || a == 4) continue;
+    const int b = opp_of(a);
+    const T w = (T)w_of(a);
+    const V k = vsplat<V>(odd_w<T>(a));
+    // c.u, c.du for the four directions 1 (1,0), 2 (0,1), 5 (1,1), 6 (-1,1)
+    V cu, cdu;
+    if (a == 1) {
+      cu = ux;
+      cdu = dux;
+    } else if (a == 2) {
+      cu = uy;
+      cdu = duy;
+    } else if (a == 5) {
+      cu = vadd(ux, uy);
+      cdu = vadd(dux, duy);
+    } else {
+      cu = vsub(uy, ux);
+      cdu = vsub(duy, dux);
+    }
+    const V csu = vadd(cu, vsplat<V>((T)cx_of(a) * c.urx + (T)cy_of(a) * c.ury));
+    const V dc = vmul(drho, cu);
+    const V X = vfma(dc, cu, vmul(cdu, csu));
+    const V P = vfma(vsplat<V>((T)4.5 * c.s_plus * w), X, vmul(vsplat<V>(c.s_plus * w), K));
+    V dp = vfma(nsph, vadd(h[a], h[b]), P);
+    // -s- (h- - heq-), h- = (h_a - h_b) / 2, heq- = k (drho c.u + c.du)
+    V dm = vmul(nsm, vsub(vmul(half, vsub(h[a], h[b])), vmul(k, vadd(dc, cdu))));
+    if (kForce) {
+      V cg;
+      if (a == 1)
+        cg = gx;
+      else if (a == 2)
+        cg = gy;
+      else if (a == 5)
+        cg = vadd(gx, gy);
+      else
+        cg = vsub(gy, gx);
+      dp = vfma(vsplat<V>(c.a_plus * w * (T)9), vmul(cu, cg), vfma(vsplat<V>(c.a_plus * w * (T)-3), ug, dp));
+      dm = vfma(vsplat<V>(c.a_minus), vmul(k, cg), dm);
+    }
+    even = vadd(even, dp);
+    o[a] = vadd(vadd(h[a], dp), dm);
+    o[b] = vsub(vadd(h[b], dp), dm);
+  }
+  o[0] = vfma(vsplat<V>((T)-2), even, h[0]);
+}
+
+// The update of fluid nodes (no penalization) in FP32: moments, velocity and
+// the collision, from the pre-collision offsets h of a node pair (or of one
+// node in both lanes); kForce adds the uniform body force.  Returns rho.
+template <typename V, bool kForce>
+__device__ __forceinline__ V fluid_update(const Lattice &L, const Consts<float> &cst,
+                                          const V (&h)[9], V (&o)[9]) {
+  const V drho = vadd(vadd(vadd(h[0], h[1]), vadd(h[2], h[3])),
+                      vadd(vadd(vadd(h[4], h[5]), vadd(h[6], h[7])), h[8]));
+  V djx = vadd(vadd(vsub(h[1], h[3]), vsub(h[5], h[6])), vsub(h[8], h[7]));
+  V djy = vadd(vadd(vsub(h[2], h[4]), vsub(h[5], h[7])), vsub(h[6], h[8]));
+  const V rho = vadd(vsplat<V>(1.0f), drho);
+  const V inv = vrcp(rho);
+  if (kForce) {
+    const V gx = vsplat<V>(lat_bf<float>(L, 0)), gy = vsplat<V>(lat_bf<float>(L, 1));
+    djx = vfma(vsplat<V>(0.5f), gx, djx);
+    djy = vfma(vsplat<V>(0.5f), gy, djy);
+    collide2<V, float, true>(h, drho, vmul(vfma(drho, vsplat<V>(-cst.urx), djx), inv),
+                             vmul(vfma(drho, vsplat<V>(-cst.ury), djy), inv), gx, gy, cst, o);
+  } else {
+    collide2<V, float, false>(h, drho, vmul(vfma(drho, vsplat<V>(-cst.urx), djx), inv),
+                              vmul(vfma(drho, vsplat<V>(-cst.ury), djy), inv), V{}, V{}, cst, o);
+  }
+  return rho;
+}
+
 // Moments, penalized velocity and force density of one node (Eqs. updatestep
 // .. updatestepm: G = -rho (chi/eta)(u - u_s) in the rearranged form
 // -(chi/eta)(j - rho u_s)/(1 + chi dt/(2 eta)), plus the body force), then
 // the collision.  Returns true for a non-finite or non-positive density.
-template <typename T>
+template <typename T, bool kPacked>
 __device__ __forceinline__ bool update_node(const T (&h)[9], uint8_t m, int i, int j,
                                             const Lattice &L, const BodyState *body,
                                             const Consts<T> &cst, T (&o)[9], T &pen_x,
                                             T &pen_y) {
   pen_x = pen_y = (T)0;  // the penalization part of G (solid nodes only)
+  if constexpr (kPacked) {
+    // 16-bit storage: the packed arithmetic of fluid_update, which the bulk
+    // kernels of these forms use, with the node in both lanes, so that a
+    // fluid node gets the same bits in either kernel
+    F2 hv[9], ov[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) hv[a] = vsame(h[a]);
+    F2 rho;
+    if (!(m & kSolid)) {
+      rho = L.has_bf ? fluid_update<F2, true>(L, cst, hv, ov) : fluid_update<F2, false>(L, cst, hv, ov);
+    } else {
+      const F2 drho = vadd(vadd(vadd(hv[0], hv[1]), vadd(hv[2], hv[3])),
+                           vadd(vadd(vadd(hv[4], hv[5]), vadd(hv[6], hv[7])), hv[8]));
+      F2 djx = vadd(vadd(vsub(hv[1], hv[3]), vsub(hv[5], hv[6])), vsub(hv[8], hv[7]));
+      F2 djy = vadd(vadd(vsub(hv[2], hv[4]), vsub(hv[5], hv[7])), vsub(hv[6], hv[8]));
+      rho = vadd(vsame(1.0f), drho);
+      const float bfx = lat_bf<float>(L, 0), bfy = lat_bf<float>(L, 1);
+      djx = vfma(vsame(0.5f), vsame(bfx), djx);
+      djy = vfma(vsame(0.5f), vsame(bfy), djy);
+      float usx, usy;
+      solid_velocity<float>(*body, i, j, usx, usy);
+      const float k = cst.half_pen, r = vlo(rho), dr = vlo(drho);
+      const float den = r + k * r;
+      // the momentum defect j - rho u_s, and u - u_ref written as
+      // (u_s - u_ref) + (j - rho u_s)/(rho (1 + k)) (see below)
+      const float defx = vlo(djx) - dr * usx + (cst.urx - usx);
+      const float defy = vlo(djy) - dr * usy + (cst.ury - usy);
+      const float dux = (usx - cst.urx) + defx / den, duy = (usy - cst.ury) + defy / den;
+      const float pen = 2.0f * k;
+      pen_x = -pen * defx / (1.0f + k);
+      pen_y = -pen * defy / (1.0f + k);
+      collide2<F2, float, true>(hv, drho, vsame(dux), vsame(duy), vsame(bfx + pen_x),
+                                vsame(bfy + pen_y), cst, ov);
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) o[a] = vlo(ov[a]);
+    return rho_bad(vlo(rho));
+  } else {
   const T drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
   const T rho = (T)1 + drho;
   // j - u_ref (the offsets' first moment; sum_a c_a E_a = u_ref)
@@ -571,6 +746,7 @@ __device__ __forceinline__ bool update_node(const T (&h)[9], uint8_t m, int i, i
                       (T)0, cst, o);
   }
   return !(rho > (T)0) || !isfinite(rho);
+  }
 }
 
 // pre-collision populations of an edge node, with the side conditions
@@ -620,7 +796,8 @@ __device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bo
     m = p.chi[node];
   }
   T o[9], pen_x, pen_y;
-  const bool bad = update_node<T>(h, m, i, j, L, p.body_src, Consts<T>(p), o, pen_x, pen_y);
+  const bool bad = update_node<T, sizeof(S) == 2>(h, m, i, j, L, p.body_src, Consts<T>(p), o, pen_x,
+                                                  pen_y);
 #pragma unroll
   for (int a = 0; a < 9; ++a) Store<S>::st(dst + (int64_t)a * L.plane + node, o[a]);
   if (in_reg && (m & kInterface)) mem_terms<T>(p, o, i, j, m, tm, acc);
@@ -787,109 +964,6 @@ __global__ void __launch_bounds__(kThreads * kTiles) bulk_kernel(const StepArgs 
 }
 
 // ---------------------------------------------------------------------------
-// two nodes at once: the 16-bit bulk kernels collide their nodes in pairs
-// with the packed f32x2 instructions of sm_100 and later (one instruction
-// for both nodes of a pair).
-// ---------------------------------------------------------------------------
-struct F2 {
-  float2 v;
-};
-__device__ __forceinline__ unsigned long long f2_bits(F2 a) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.v.x), "f"(a.v.y));
-  return r;
-}
-__device__ __forceinline__ F2 bits_f2(unsigned long long r) {
-  F2 a;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.v.x), "=f"(a.v.y) : "l"(r));
-  return a;
-}
-__device__ __forceinline__ F2 vpair(float x, float y) { return F2{make_float2(x, y)}; }
-__device__ __forceinline__ F2 vsplat(float c) { return F2{make_float2(c, c)}; }
-__device__ __forceinline__ F2 vadd(F2 a, F2 b) { return F2{__fadd2_rn(a.v, b.v)}; }
-__device__ __forceinline__ F2 vmul(F2 a, F2 b) { return F2{__fmul2_rn(a.v, b.v)}; }
-__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return F2{__ffma2_rn(a.v, b.v, c.v)}; }
-__device__ __forceinline__ F2 vsub(F2 a, F2 b) {
-  unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
-  return bits_f2(r);
-}
-__device__ __forceinline__ F2 vrcp(F2 a) { return vpair(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
-__device__ __forceinline__ float vlo(F2 a) { return a.v.x; }
-__device__ __forceinline__ float vhi(F2 a) { return a.v.y; }
-
-// The collision of collide() for two nodes, with the relaxation rate and
-// weights folded into the even part's coefficients: for each pair
-// (a, opp(a))
-//   s+ heq+ = s+ w K + 4.5 s+ w X,  X = drho (c.u)^2 + (c.du)(c.u + c.u_ref),
-//   K = drho (1 - 1.5 |u|^2) - 1.5 (|u|^2 - |u_ref|^2),
-// the same terms as heq_a = w_a [drho (1 + Q_a(u)) + Q_a(u) - Q_a(u_ref)].  The
-// odd part keeps collide()'s form -s- (h- - k (drho c.u + c.du)) with the
-// coefficients k of odd_w (its momentum is then exact: a folded s- k would
-// round differently from s-), and the rest population takes the even
-// changes' remainder as in collide().
-template <typename V, typename T, bool kForce>
-__device__ __forceinline__ void collide2(const V (&h)[9], V drho, V dux, V duy, V gx, V gy,
-                                         const Consts<T> &c, V (&o)[9]) {
-  const V urx = vsplat(c.urx), ury = vsplat(c.ury);
-  const V ux = vadd(urx, dux), uy = vadd(ury, duy);
-  const V uu = vfma(ux, ux, vmul(uy, uy));
-  const V dsu = vfma(dux, vadd(ux, urx), vmul(duy, vadd(uy, ury)));
-  const V m15 = vsplat((T)-1.5);
-  const V K = vfma(m15, dsu, vmul(drho, vfma(m15, uu, vsplat((T)1))));
-  V ug{};
-  if (kForce) ug = vfma(ux, gx, vmul(uy, gy));
-  const V nsph = vsplat((T)-0.5 * c.s_plus), nsm = vsplat(-c.s_minus), half = vsplat((T)0.5);
-  V even = vsplat((T)0);
-#pragma unroll
-  for (int a = 1; a <= 6; ++a) {
-    if (a == 3 || a == 4) continue;
-    const int b = opp_of(a);
-    const T w = (T)w_of(a);
-    const V k = vsplat(odd_w<T>(a));
-    // c.u, c.du for the four directions 1 (1,0), 2 (0,1), 5 (1,1), 6 (-1,1)
-    V cu, cdu;
-    if (a == 1) {
-      cu = ux;
-      cdu = dux;
-    } else if (a == 2) {
-      cu = uy;
-      cdu = duy;
-    } else if (a == 5) {
-      cu = vadd(ux, uy);
-      cdu = vadd(dux, duy);
-    } else {
-      cu = vsub(uy, ux);
-      cdu = vsub(duy, dux);
-    }
-    const V csu = vadd(cu, vsplat((T)cx_of(a) * c.urx + (T)cy_of(a) * c.ury));
-    const V dc = vmul(drho, cu);
-    const V X = vfma(dc, cu, vmul(cdu, csu));
-    const V P = vfma(vsplat((T)4.5 * c.s_plus * w), X, vmul(vsplat(c.s_plus * w), K));
-    V dp = vfma(nsph, vadd(h[a], h[b]), P);
-    // -s- (h- - heq-), h- = (h_a - h_b) / 2, heq- = k (drho c.u + c.du)
-    V dm = vmul(nsm, vsub(vmul(half, vsub(h[a], h[b])), vmul(k, vadd(dc, cdu))));
-    if (kForce) {
-      V cg;
-      if (a == 1)
-        cg = gx;
-      else if (a == 2)
-        cg = gy;
-      else if (a == 5)
-        cg = vadd(gx, gy);
-      else
-        cg = vsub(gy, gx);
-      dp = vfma(vsplat(c.a_plus * w * (T)9), vmul(cu, cg), vfma(vsplat(c.a_plus * w * (T)-3), ug, dp));
-      dm = vfma(vsplat(c.a_minus), vmul(k, cg), dm);
-    }
-    even = vadd(even, dp);
-    o[a] = vadd(vadd(h[a], dp), dm);
-    o[b] = vsub(vadd(h[b], dp), dm);
-  }
-  o[0] = vfma(vsplat((T)-2), even, h[0]);
-}
-
-// ---------------------------------------------------------------------------
 // bulk kernel for 16-bit storage: eight nodes per thread.  HBM stays busy
 // only with enough bytes in flight per SM, and a thread holds what it loads
 // in registers until it is used; with 2-byte values the registers, not the
@@ -935,40 +1009,21 @@ __device__ __forceinline__ uint32_t shift16(uint32_t a, uint32_t b) {
   return __funnelshift_r(a, b, 16);
 }
 
-// the collision of the node pair whose pre-collision values are the packed
+// the update of the node pair whose pre-collision values are the packed
 // words w[a]; returns the packed post-collision words and rho
 template <typename S, bool kForce>
 __device__ __forceinline__ F2 collide_pair16(const StepArgs &p, const uint32_t (&w)[9],
                                              uint32_t (&out)[9]) {
   using P = Pair16<S>;
-  const Lattice &L = p.L;
-  const Consts<float> cst(p);
   F2 h[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) h[a] = vpair(P::lo(w[a]), P::hi(w[a]));
-  const F2 drho = vadd(vadd(vadd(h[0], h[1]), vadd(h[2], h[3])),
-                       vadd(vadd(vadd(h[4], h[5]), vadd(h[6], h[7])), h[8]));
-  F2 djx = vadd(vadd(vsub(h[1], h[3]), vsub(h[5], h[6])), vsub(h[8], h[7]));
-  F2 djy = vadd(vadd(vsub(h[2], h[4]), vsub(h[5], h[7])), vsub(h[6], h[8]));
-  const F2 rho = vadd(vsplat(1.0f), drho);
-  const F2 inv = vrcp(rho);
   F2 o[9];
-  if (kForce) {
-    const F2 gx = vsplat(lat_bf<float>(L, 0)), gy = vsplat(lat_bf<float>(L, 1));
-    djx = vfma(vsplat(0.5f), gx, djx);
-    djy = vfma(vsplat(0.5f), gy, djy);
-    collide2<F2, float, true>(h, drho, vmul(vfma(drho, vsplat(-cst.urx), djx), inv),
-                              vmul(vfma(drho, vsplat(-cst.ury), djy), inv), gx, gy, cst, o);
-  } else {
-    collide2<F2, float, false>(h, drho, vmul(vfma(drho, vsplat(-cst.urx), djx), inv),
-                               vmul(vfma(drho, vsplat(-cst.ury), djy), inv), F2{}, F2{}, cst, o);
-  }
+  const F2 rho = fluid_update<F2, kForce>(p.L, Consts<float>(p), h, o);
 #pragma unroll
   for (int a = 0; a < 9; ++a) out[a] = P::pack(vlo(o[a]), vhi(o[a]));
   return rho;
 }
-
-__device__ __forceinline__ bool rho_bad(float r) { return !(r > 0.f) || !isfinite(r); }
 
 template <typename S, bool kForce, int kMinBlocks>
 __global__ void __launch_bounds__(32, kMinBlocks) bulk16_kernel(const StepArgs p) {

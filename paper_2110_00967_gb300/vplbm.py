@@ -94,6 +94,7 @@ _SIGS = [
     ("vplbm_set_stream", [_vp, _vp], C.c_int),
     ("vplbm_set_body", [_vp, _P(vplbm_body)], C.c_int),
     ("vplbm_step", [_vp, C.c_int32], C.c_int),
+    ("vplbm_prepare", [_vp, C.c_int32], C.c_int),
     ("vplbm_force_mem", [_vp, _P(C.c_double), _P(C.c_double)], C.c_int),
     ("vplbm_force_sim", [_vp, _P(C.c_double), _P(C.c_double)], C.c_int),
     ("vplbm_force_angot", [_vp, _P(C.c_double), _P(C.c_double)], C.c_int),
@@ -122,6 +123,7 @@ _SIGS = [
     ("vplbm_bulk_variant", [_vp, _P(C.c_int32)], C.c_int),
     ("vplbm_batch_create", [_P(_vp), C.c_int32, _vp, _P(_vp)], C.c_int),
     ("vplbm_batch_step", [_vp, C.c_int32], C.c_int),
+    ("vplbm_batch_prepare", [_vp, C.c_int32], C.c_int),
     ("vplbm_batch_autotune", [_vp, C.c_int32, _P(C.c_int32)], C.c_int),
     ("vplbm_batch_destroy", [_vp], None),
     ("vplbm_sim_force_static", [_P(vplbm_config), _vp, _vp, C.c_int32, _P(C.c_double),
@@ -187,6 +189,10 @@ def vplbm_set_body(ctx, b: vplbm_body):
 
 def vplbm_step(ctx, nsteps: int):
     _check(lib().vplbm_step(ctx, nsteps), ctx)
+
+
+def vplbm_prepare(ctx, nsteps: int):
+    _check(lib().vplbm_prepare(ctx, nsteps), ctx)
 
 
 def _force(fn, ctx):
@@ -349,6 +355,10 @@ def vplbm_batch_step(batch, nsteps: int):
     _check(lib().vplbm_batch_step(batch, nsteps))
 
 
+def vplbm_batch_prepare(batch, nsteps: int):
+    _check(lib().vplbm_batch_prepare(batch, nsteps))
+
+
 def vplbm_batch_autotune(batch, trials: int = 20) -> int:
     v = C.c_int32()
     _check(lib().vplbm_batch_autotune(batch, trials, C.byref(v)))
@@ -426,6 +436,9 @@ class Lattice:
 
     def step(self, n: int = 1):
         vplbm_step(self.ctx, n)
+
+    def prepare(self, n: int):
+        vplbm_prepare(self.ctx, n)
 
     def force_mem(self):
         return vplbm_force_mem(self.ctx)
@@ -554,6 +567,9 @@ class Batch:
 
     def step(self, n: int = 1):
         vplbm_batch_step(self.handle, n)
+
+    def prepare(self, n: int):
+        vplbm_batch_prepare(self.handle, n)
 
     def autotune(self, trials: int = 20) -> int:
         return vplbm_batch_autotune(self.handle, trials)

@@ -160,3 +160,36 @@ def test_runs_of_any_length_equal_single_steps(lengths):
     same_state(ref, member, total)
     same_state(other_ref, other, total)
     batch.close()
+
+
+def test_prepared_lengths_replay_one_graph_and_change_nothing():
+    """vplbm_prepare / vplbm_batch_prepare capture the graph of a 20-step run:
+    the run then replays one graph per lattice (2 * 20 + 1 launches instead of
+    the 42 of 16 + 4), and the lattices end bit-identical to unprepared ones
+    stepped the same way, for a lattice alone and in a batch."""
+    w = W.naca(7.0, dtype="f32", nx=256, ny=128)
+    plain, prepared = lattice(w), lattice(w)
+    for lat in (plain, prepared):
+        lat.step(1)  # the first step (pre-collision state)
+    prepared.prepare(20)
+    l0, l1 = plain.launches, prepared.launches
+    plain.step(20)
+    prepared.step(20)
+    assert plain.launches - l0 == (2 * 16 + 1) + (2 * 4 + 1)
+    assert prepared.launches - l1 == 2 * 20 + 1
+    same_state(plain, prepared, 21)
+    # in a batch, and across a change of the bulk kernel's launch form
+    members = [lattice(w), lattice(W.disk_channel())]
+    alone = [lattice(w), lattice(W.disk_channel())]
+    batch = V.Batch(members)
+    batch.step(1)
+    batch.prepare(20)
+    for m in members:
+        m.bulk_variant = 1  # drops the graphs; the prepared length is captured again
+    batch.step(52)  # 32 + 20
+    for a in alone:
+        a.bulk_variant = 1
+        a.step(53)
+    for a, m in zip(alone, members):
+        same_state(a, m, 53)
+    batch.close()

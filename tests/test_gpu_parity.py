@@ -524,13 +524,16 @@ def test_first_order_sim_per_step(case):
     assert np.abs(ref0[:, :2] - ref[:, :2]).max() > 10 * err
 
 
-def test_sim_point_counts_share_the_flow():
-    """SIM with 213, 849 and 3393 points on a fixed NACA body (FP32, 512 x 256,
-    12 degrees): the lattices carry bit-identical flows and MEM forces (SIM
-    does not feed back), and each SIM history matches the oracle's SIM over the
-    same polygon, step by step, within 1e-3 of its largest value."""
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_sim_point_counts_share_the_flow(dtype):
+    """SIM with 213, 849 and 3393 points on a fixed NACA body (512 x 256, 12
+    degrees): the lattices carry bit-identical flows and MEM forces (SIM does
+    not feed back; the point counts give slightly different force regions,
+    so nodes move between the special and the bulk kernel), and with FP32
+    storage each SIM history matches the oracle's SIM over the same polygon,
+    step by step, within 1e-3 of its largest value."""
     import dataclasses
-    base = W.naca(12.0, dtype="f32", nx=512, ny=256)
+    base = W.naca(12.0, dtype=dtype, nx=512, ny=256)
     n = 120
     runs = []
     for npts in (213, 849, 3393):
@@ -543,6 +546,8 @@ def test_sim_point_counts_share_the_flow():
         for a, b in zip(lat.get_fields(), f0):
             assert np.array_equal(a, b)
         np.testing.assert_array_equal(lat.history(V.MEM, n), runs[0][1].history(V.MEM, n))
+    if dtype != "f32":
+        return
     for w, lat in runs:
         got = lat.history(V.SIM, n)
         cfg, body, chi, f, pts = oracle_setup(w)
