@@ -8,7 +8,8 @@ collide-penalize-stream kernel with the MEM force and the SIM force (849
 points) of that step.  Metric: million lattice-node updates per second
 (MLUPS) over all lattices and ranks.  The five lattices hold 5 x 151 MB of
 populations, more than the 129 MB L2, and are stepped in turn as one batch
-(vplbm_batch_step: 32 steps of all five replayed from one CUDA graph).
+(vplbm_batch_step: each lattice replays its own CUDA graphs of up to 32
+steps on a stream of its own).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,17 +39,20 @@ ANGLES = (0.0, 5.0, 10.0, 15.0, 20.0)
 NX, NY = 2048, 1024
 # populations read once and written once per node: 9 x 4 B + 9 x 4 B for FP32 storage,
 # 9 x 2 B + 9 x 2 B for the 16-bit offset forms
-BYTES_PER_LUP = {"f32": 72, "f16": 36, "bf16": 36}
-STORAGE_NAME = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}
+BYTES_PER_LUP = {"f32": 72, "f16": 36, "bf16": 36, "f16sr": 36, "bf16sr": 36}
+STORAGE_NAME = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16", "f16sr": "__half",
+                "bf16sr": "__nv_bfloat16"}
 # the arithmetic of the step: FP32, with the 16-bit forms storing FP16 / BF16
 # offsets and colliding in FP32 (force sums FP64 in every form)
-DTYPE_NAME = {"f32": "f32", "f16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute"}
+DTYPE_NAME = {"f32": "f32", "f16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute",
+              "f16sr": "f16-storage-stochastic/f32-compute",
+              "bf16sr": "bf16-storage-stochastic/f32-compute"}
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_naca2048_f32.md")
 KERNEL_SOURCES = ("paper_2110_00967_gb300/csrc/step.cu",
                   "paper_2110_00967_gb300/csrc/vplbm_internal.cuh",
                   "paper_2110_00967_gb300/csrc/api.cu")
 METRIC = "VP-LBM MLUPS"
-CHUNK = 32  # steps per graph replay of the batch
+CHUNK = 32  # the longest step graph of a lattice
 HISTORY = 64  # force-history ring of each lattice
 def workload_name(dtype: str) -> str:
     return f"naca0012-re1000-2048x1024-{dtype}-alpha0,5,10,15,20"
@@ -235,11 +239,11 @@ def run_ours(args, rank, world, local_rank):
     lats = [V.Lattice(V.config_of(w, history_len=HISTORY), device=dev) for w in works]
     for w, lat in zip(works, lats):
         lat.set_body(V.body_of(w))
-    # the five lattices advance in lockstep, 32-step runs replayed from one graph
+    # the five lattices advance in lockstep, each replaying its own step graphs
     batch = V.Batch(lats, stream=stream)
-    # the bulk kernel's launch form, timed with the five lattices side by side,
-    # before the warm-up
-    variants = [batch.autotune(64)]
+    # the bulk kernel's launch form per size class (one class here), timed
+    # with the five lattices side by side, before the warm-up
+    variants = batch.autotune(64) if not args.no_tune else [lat.bulk_variant for lat in lats]
     # the step graphs of a run of args.steps steps, captured before the timed
     # region (one graph per lattice for up to 32 steps)
     batch.prepare(args.steps)
@@ -359,6 +363,7 @@ def run_sedimentation(args, rank, world, local_rank, paper=False):
     for w, lat in zip(works, lats):
         lat.set_body(V.body_of(w))
     batch = V.Batch(lats, stream=stream)
+    batch.prepare(args.steps)
     batch.step(args.warmup)
     torch.cuda.synchronize()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -369,10 +374,14 @@ def run_sedimentation(args, rank, world, local_rank, paper=False):
     if clocks:
         clocks.start()
         time.sleep(0.3)
+    if args.profile_range:
+        torch.cuda.profiler.start()
     start.record(stream)
     batch.step(args.steps)
     end.record(stream)
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     clk = clocks.stop() if clocks else None
     barrier(world)
     elapsed_ms = reduce_max(start.elapsed_time(end), world, dev)
@@ -427,30 +436,31 @@ def run_sedimentation(args, rank, world, local_rank, paper=False):
 
 def run_serving(args, rank, world, local_rank):
     """A seeded mix of NACA 0012 solves served to convergence (continuous
-    batching under a memory budget); Poisson arrivals at 4 / (estimated mean
-    solve time of one request alone).  `value` counts converged solves only;
-    requests stopped at the step cap are reported apart."""
+    batching under a memory budget).  Poisson arrivals at 4 / (mean
+    single-instance solve time), the solve time measured first: one 1024 x 512
+    request at 10 degrees in FP32, alone, run window by window to convergence
+    and scaled to the mix's mean grid size; the same arrival rate for every
+    storage form and for the one-at-a-time comparison.  `value` counts
+    converged solves only; requests stopped at the step cap are reported
+    apart."""
     import torch
     from paper_2110_00967_gb300 import serve as S
     from paper_2110_00967_gb300 import vplbm as V
     from paper_2110_00967_gb300 import workloads as W
 
     torch.cuda.set_device(local_rank)
-    backend = S.GpuBackend(args.dtype, device=torch.device("cuda", local_rank))
-    # calibration: one 1024 x 512 request alone for two windows
-    probe = W.Request(-1, 0.0, 10.0, 1024, 512)
-    lat = backend.make(probe)
-    b = backend.batch([lat])
-    b.step(1000)
+    dev = torch.device("cuda", local_rank)
+    backend = S.GpuBackend(args.dtype, device=dev, tune_trials=args.tune_trials)
+    # calibration: the single-instance FP32 solve time of a mid-size request
+    cal = S.Server(S.GpuBackend("f32", device=dev), memory_bytes=args.memory_gb << 30,
+                   window=1000, tol=1e-4, cap=args.cap, max_active=1)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    b.step(1000)
+    (cal_res,) = cal.run([W.Request(-1, 0.0, 10.0, 1024, 512)])
     torch.cuda.synchronize()
-    t_window = time.perf_counter() - t
-    b.close()
-    lat.close()
+    t_cal = time.perf_counter() - t
     mean_nodes = sum(nx * ny for nx, ny in W.SERVING_GRIDS) / len(W.SERVING_GRIDS)
-    solve_s = t_window * (mean_nodes / (1024 * 512)) * (args.cap / 1000)
+    solve_s = t_cal * mean_nodes / (1024 * 512)
     rate = 4.0 / solve_s
     reqs = W.serving_requests(args.requests, rate=rate)
     srv = S.Server(backend, memory_bytes=args.memory_gb << 30, window=1000, tol=1e-4,
@@ -470,9 +480,16 @@ def run_serving(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.dtype], "data": "synthetic",
         "config": {"workload": f"naca0012-serving-{args.requests}req-seed2110-{args.dtype}",
                    "grids": [list(g) for g in W.SERVING_GRIDS], "alpha_deg": [0, 20],
-                   "arrival_rate_per_s": round(rate, 4), "window": 1000, "tol": 1e-4,
+                   "arrival_rate_per_s": round(rate, 4),
+                   "calibration": {"request": "1024x512 alpha 10 f32 alone",
+                                   "steps": cal_res.steps, "converged": cal_res.converged,
+                                   "seconds": round(t_cal, 4),
+                                   "mean_solve_s_estimate": round(solve_s, 4)},
+                   "window": 1000, "tol": 1e-4,
                    "cap_steps": args.cap, "memory_budget_gb": args.memory_gb,
                    "max_active": args.max_active or "memory-bound",
+                   "bulk_forms": ({f"{k[0]}x{k[1]}": v for k, v in sorted(backend.forms.items())}
+                                  if args.tune_trials else "default"),
                    "parallelism": f"replicas{world}"},
         "p50_s": round(summ["p50_s"], 4), "p99_s": round(summ["p99_s"], 4),
         "latency": "arrival to converged Cd/Cl, converged requests only",
@@ -735,6 +752,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch form instead of tuning it first (fewer "
+                         "launches ahead of a profiled region)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed region with cudaProfilerStart/Stop (for ncu's "
                          "application-range replay, which measures the concurrent kernels "
@@ -754,11 +774,15 @@ def main(argv=None):
     ap.add_argument("--requests", type=int, default=256, help="serving: number of requests")
     ap.add_argument("--cap", type=int, default=200000, help="serving: step cap per request")
     ap.add_argument("--memory-gb", type=int, default=40, help="serving: device-memory budget")
+    ap.add_argument("--tune-trials", type=int, default=16,
+                    help="serving: timed steps per launch form when a grid size is first "
+                         "seen (0: the default form everywhere)")
     ap.add_argument("--max-active", type=int, default=0,
                     help="serving: most requests stepped at once (0: as many as fit; 1: one "
                          "request at a time, the single-instance comparison)")
-    ap.add_argument("--dtype", choices=("f32", "f16", "bf16"), default="f32",
-                    help="population storage: FP32, or FP16/BF16 offsets (FP32 collision)")
+    ap.add_argument("--dtype", choices=("f32", "f16", "bf16", "f16sr", "bf16sr"), default="f32",
+                    help="population storage: FP32, or FP16/BF16 offsets (FP32 collision), "
+                         "rounded to nearest or (the sr forms) stochastically")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -48,11 +48,24 @@ typedef enum {
 
 /* Storage of the populations.  All forms store offsets h_a = f_a - E_a from
  * E_a = feq_a(1, u_ref) (config.u_ref; zero gives the lattice weights w_a).
- * F64 computes in FP64; F32, F16_OFS and BF16_OFS compute the step in FP32
- * (the 16-bit forms round to nearest even on store).  Force sums are exact
+ * F64 computes in FP64; the others compute the step in FP32.  F16_OFS and
+ * BF16_OFS round each stored value to nearest even; F16_SR and BF16_SR round
+ * it stochastically: up or down with probabilities in proportion to its
+ * distances from the two neighbouring 16-bit values, drawn from a counter-
+ * based hash of the lattice's step count, the node and the population
+ * (reproducible run to run).  Rounding to nearest leaves a steady flow in a
+ * quantized state offset from the exact one, which time averages keep;
+ * stochastic rounding has no such offset on average.  Force sums are exact
  * 64-bit fixed-point integers converted to FP64; the rigid-body update is
  * FP64 in every form. */
-typedef enum { VPLBM_F64 = 0, VPLBM_F32 = 1, VPLBM_F16_OFS = 2, VPLBM_BF16_OFS = 3 } vplbm_dtype;
+typedef enum {
+  VPLBM_F64 = 0,
+  VPLBM_F32 = 1,
+  VPLBM_F16_OFS = 2,
+  VPLBM_BF16_OFS = 3,
+  VPLBM_F16_SR = 4,
+  VPLBM_BF16_SR = 5
+} vplbm_dtype;
 
 /* Collision operator: BGK (Sec. 2.2) or TRT (Eq. TRT) with
  * tau- = Lambda / (tau+ - 1/2) + 1/2. */
@@ -369,12 +382,21 @@ vplbm_status vplbm_batch_step(vplbm_batch *batch, int32_t nsteps);
  * stream).  ESTATE when a lattice has no body placed. */
 vplbm_status vplbm_batch_prepare(vplbm_batch *batch, int32_t nsteps);
 
-/* The bulk kernel's launch form for every lattice of the batch, timed on the
- * batch's own steps as vplbm_autotune does for one lattice (the same form on
- * every lattice, 9 * (32 + trials) batch steps, events on the batch's
- * stream).  The fastest form is set on every lattice and written to *variant
- * (may be NULL).  ESTATE when a lattice has no body placed. */
-vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int32_t trials, int32_t *variant);
+/* The bulk kernel's launch form per lattice of the batch, timed on the
+ * batch's own steps.  Lattices of one size (nx, ny) and storage type form a
+ * class and share a form.  Three passes visit the classes in turn; for one
+ * class every form runs 32 untimed batch steps (its step graphs are captured
+ * there) and then `trials` batch steps timed with CUDA events on the batch's
+ * stream (1 <= trials <= 10000), the other classes held at their current
+ * forms, and the class keeps the form with the fastest time seen so far.
+ * With one class this is vplbm_autotune on the whole batch.  The batch
+ * advances by 9 * G * (32 + trials) steps (G classes), which give every
+ * lattice the state, histories and sums of that many vplbm_batch_step steps
+ * (the forms agree bit for bit).  variants: host array of n entries that
+ * receives each lattice's form, in the order of vplbm_batch_create (may be
+ * NULL).  Synchronises the batch's stream.  ESTATE when a lattice has no body
+ * placed. */
+vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int32_t trials, int32_t *variants);
 
 /* Releases the batch (never its contexts).  NULL is accepted. */
 void vplbm_batch_destroy(vplbm_batch *batch);

@@ -40,14 +40,16 @@ size_t elem_bytes(int dtype) {
     case VPLBM_F64: return 8;
     case VPLBM_F32: return 4;
     case VPLBM_F16_OFS:
-    case VPLBM_BF16_OFS: return 2;
+    case VPLBM_BF16_OFS:
+    case VPLBM_F16_SR:
+    case VPLBM_BF16_SR: return 2;
   }
   return 0;
 }
 
 struct Layout {
   size_t buf[2], prev[2], chi, sim_pts, sim_nodes, hist, body[2], region[2], sums, counts,
-      dev_step, ticket, status, acc, total;
+      dev_step, ticket, status, acc, rng, total;
 };
 
 int effective_max_sim(const vplbm_config &c) { return c.max_sim_points > 0 ? c.max_sim_points : 4096; }
@@ -92,6 +94,7 @@ Layout make_layout(const vplbm_config &c) {
   l.ticket = take(sizeof(unsigned int));
   l.status = take(sizeof(int32_t));
   l.acc = take(2 * kAccWords * sizeof(unsigned long long));  // by step parity
+  l.rng = take(2 * sizeof(unsigned long long));                // rounding counter, by parity
   l.total = off;
   return l;
 }
@@ -225,6 +228,7 @@ struct vplbm_ctx {
   uint8_t *chi;
   SimPoint *sim_pts;
   unsigned long long *acc;
+  unsigned long long *rng;
   int32_t *sim_nodes;
   double *hist;
   BodyState *body[2];
@@ -335,6 +339,9 @@ StepArgs step_args(vplbm_ctx *c, int src, bool do_sim) {
   a.region_slots = c->region_slots;
   a.region_capacity = kRegionCapacity;
   a.raster = c->body_host.moving ? 1 : 0;
+  a.sr = stochastic_dtype(c->cfg.dtype) ? 1 : 0;
+  a.rng_src = c->rng + src;
+  a.rng_dst = c->rng + (1 - src);
   return a;
 }
 
@@ -356,7 +363,7 @@ cudaError_t flush_forces(vplbm_ctx *c, cudaStream_t s) {
   a.prev_sim = c->pending_sim ? 1 : 0;
   c->pending = false;
   ++c->launches;
-  return launch_finalize(c->cfg.dtype, a, s);
+  return launch_finalize(storage_dtype(c->cfg.dtype), a, s);
 }
 
 // A moving body's steps leave chi one time level behind the body (each step
@@ -376,7 +383,7 @@ cudaError_t queue_step(vplbm_ctx *c, cudaStream_t s, int src, bool pre, bool do_
     StepArgs a = step_args(c, src, do_sim);
     a.all_tiles = 1;
     ++c->launches;
-    if (e == cudaSuccess) e = launch_special(c->cfg.dtype, false, a, s);
+    if (e == cudaSuccess) e = launch_special(storage_dtype(c->cfg.dtype), false, a, s);
     return e;
   }
   StepArgs a = step_args(c, src, do_sim);
@@ -389,9 +396,9 @@ cudaError_t queue_step(vplbm_ctx *c, cudaStream_t s, int src, bool pre, bool do_
   a.prev_sim = c->pending_sim ? 1 : 0;
   cudaError_t e = cudaEventRecord(c->ev_fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-  if (e == cudaSuccess) e = launch_special(c->cfg.dtype, true, a, c->side);
+  if (e == cudaSuccess) e = launch_special(storage_dtype(c->cfg.dtype), true, a, c->side);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
-  if (e == cudaSuccess) e = launch_bulk(c->cfg.dtype, c->bulk_variant, a, s);
+  if (e == cudaSuccess) e = launch_bulk(storage_dtype(c->cfg.dtype), c->bulk_variant, a, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
   c->launches += 2;
   c->pending = a.defer != 0;
@@ -592,6 +599,7 @@ vplbm_status vplbm_create(const vplbm_config *cfg, void *dev_workspace, size_t b
   c->chi = (uint8_t *)(c->ws + lay.chi);
   c->sim_pts = (SimPoint *)(c->ws + lay.sim_pts);
   c->acc = (unsigned long long *)(c->ws + lay.acc);
+  c->rng = (unsigned long long *)(c->ws + lay.rng);
   c->sim_nodes = (int32_t *)(c->ws + lay.sim_nodes);
   c->hist = (double *)(c->ws + lay.hist);
   c->body[0] = (BodyState *)(c->ws + lay.body[0]);
@@ -808,7 +816,7 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
                                    std::min(L.nx - 1, i1 + 1), std::min(L.ny - 1, j1 + 1), s));
     c->launches += 2;
   }
-  VPLBM_CUDA(c, launch_init(c->cfg.dtype, L, c->body[0], c->chi, c->buf[0], c->cfg.u_in[0], c->cfg.u_in[1], s));
+  VPLBM_CUDA(c, launch_init(storage_dtype(c->cfg.dtype), L, c->body[0], c->chi, c->buf[0], c->cfg.u_in[0], c->cfg.u_in[1], s));
   ++c->launches;
   // histories, sums, counters, status
   VPLBM_CUDA(c, cudaMemsetAsync(c->ws + c->lay.hist, 0, c->lay.body[0] - c->lay.hist, s));
@@ -1003,7 +1011,7 @@ vplbm_status vplbm_get_f_dev(vplbm_ctx *c, double *f_dev) {
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!f_dev) return fail(c, VPLBM_EINVAL, "f_dev is NULL");
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "no state yet");
-  VPLBM_CUDA(c, launch_get_f(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], f_dev, 0,
+  VPLBM_CUDA(c, launch_get_f(storage_dtype(c->cfg.dtype), !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], f_dev, 0,
                              9, 0, c->L.ny, c->stream));
   ++c->launches;
   return VPLBM_OK;
@@ -1014,7 +1022,7 @@ vplbm_status vplbm_get_fields_dev(vplbm_ctx *c, double *rho, double *ux, double 
   if (!c) return fail(nullptr, VPLBM_EINVAL, "ctx is NULL");
   if (!rho || !ux || !uy) return fail(c, VPLBM_EINVAL, "NULL output");
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "no state yet");
-  VPLBM_CUDA(c, launch_get_fields(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], c->chi,
+  VPLBM_CUDA(c, launch_get_fields(storage_dtype(c->cfg.dtype), !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], c->chi,
                                   c->body[c->cur], c->half_pen, rho, ux, uy, 0, c->L.ny, c->stream));
   ++c->launches;
   return VPLBM_OK;
@@ -1067,7 +1075,7 @@ vplbm_status vplbm_get_f(vplbm_ctx *c, double *f) {
   for (int a0 = 0; a0 < 9; a0 += na)
     for (int j0 = 0; j0 < ny; j0 += rows) {
       const int r = std::min(rows, ny - j0);
-      VPLBM_CUDA(c, launch_get_f(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], st, a0,
+      VPLBM_CUDA(c, launch_get_f(storage_dtype(c->cfg.dtype), !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], st, a0,
                                  na, j0, r, c->stream));
       ++c->launches;
       const size_t w = (size_t)r * nx * sizeof(double);
@@ -1091,7 +1099,7 @@ vplbm_status vplbm_get_fields(vplbm_ctx *c, double *rho, double *ux, double *uy)
   for (int j0 = 0; j0 < ny; j0 += rows) {
     const int r = std::min(rows, ny - j0);
     const size_t m = (size_t)r * nx;
-    VPLBM_CUDA(c, launch_get_fields(c->cfg.dtype, !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], c->chi,
+    VPLBM_CUDA(c, launch_get_fields(storage_dtype(c->cfg.dtype), !c->pre, c->L, c->buf[c->cur], c->prev[c->cur], c->chi,
                                     c->body[c->cur], c->half_pen, st, st + m, st + 2 * m, j0, r,
                                     c->stream));
     ++c->launches;
@@ -1128,10 +1136,10 @@ vplbm_status vplbm_set_state(vplbm_ctx *c, const double *f_dev, const double *pr
   if (!c->has_body) return fail(c, VPLBM_ESTATE, "place a body first");
   if (post_collision && c->cfg.bc[1] == VPLBM_OUTLET_CONVECTIVE && !prev_dev)
     return fail(c, VPLBM_EINVAL, "the convective outlet needs the previous pre-collision field");
-  VPLBM_CUDA(c, launch_set_state(c->cfg.dtype, c->L, f_dev, c->buf[c->cur], c->stream));
+  VPLBM_CUDA(c, launch_set_state(storage_dtype(c->cfg.dtype), c->L, f_dev, c->buf[c->cur], c->stream));
   ++c->launches;
   if (post_collision && prev_dev) {
-    VPLBM_CUDA(c, launch_set_prev(c->cfg.dtype, c->L, prev_dev, c->prev[c->cur], c->stream));
+    VPLBM_CUDA(c, launch_set_prev(storage_dtype(c->cfg.dtype), c->L, prev_dev, c->prev[c->cur], c->stream));
     ++c->launches;
   }
   c->pre = post_collision == 0;
@@ -1160,7 +1168,7 @@ struct SnapHeader {
   uint64_t tail_bytes, pop_bytes;
 };
 constexpr char kSnapMagic[8] = {'V', 'P', 'L', 'B', 'M', 'S', 'N', 'P'};
-constexpr int32_t kSnapVersion = 1;
+constexpr int32_t kSnapVersion = 2;
 
 size_t snap_header_bytes() { return align_up(sizeof(SnapHeader), 64); }
 size_t snap_tail_bytes(const vplbm_ctx *c) { return c->lay.total - c->lay.prev[0]; }
@@ -1448,27 +1456,52 @@ vplbm_status vplbm_batch_create(vplbm_ctx *const *ctxs, int32_t n, void *cuda_st
   return VPLBM_OK;
 }
 
-vplbm_status vplbm_batch_autotune(vplbm_batch *b, int32_t trials, int32_t *variant) {
+vplbm_status vplbm_batch_autotune(vplbm_batch *b, int32_t trials, int32_t *variants) {
   Range range_("vplbm_batch_autotune");
   if (!b) return batch_fail(VPLBM_EINVAL, "vplbm_batch_autotune: batch is NULL");
   if (trials < 1 || trials > 10000)
     return batch_fail(VPLBM_EINVAL, "vplbm_batch_autotune: trials must be in 1 .. 10000");
-  float t[kBulkVariants];
-  for (int r = 0; r < kTuneRounds; ++r)
-    for (int v = 0; v < kBulkVariants; ++v) {
-      for (vplbm_ctx *c : b->ctxs) set_variant(c, v);
-      if (vplbm_status st = vplbm_batch_step(b, kGraphMax)) return st;
-      float ms = 0.f;
-      if (vplbm_status st = timed(b->stream, trials, &ms, [&] { return vplbm_batch_step(b, trials); },
-                                  nullptr))
-        return st;
-      t[v] = r == 0 ? ms : std::min(t[v], ms);
+  const int n = (int)b->ctxs.size();
+  for (int k = 0; k < n; ++k)
+    if (!b->ctxs[k]->has_body)
+      return batch_fail(VPLBM_ESTATE, fmt("vplbm_batch_autotune: lattice %d has no body placed", k));
+  // classes: lattices of one size and storage form share a launch form
+  std::vector<int> cls(n, -1);
+  int ncls = 0;
+  for (int k = 0; k < n; ++k) {
+    const vplbm_config &a = b->ctxs[k]->cfg;
+    for (int q = 0; q < k && cls[k] < 0; ++q) {
+      const vplbm_config &o = b->ctxs[q]->cfg;
+      if (o.nx == a.nx && o.ny == a.ny && o.dtype == a.dtype) cls[k] = cls[q];
     }
-  int best = 0;
-  for (int v = 1; v < kBulkVariants; ++v)
-    if (t[v] < t[best]) best = v;
-  for (vplbm_ctx *c : b->ctxs) set_variant(c, best);
-  if (variant) *variant = best;
+    if (cls[k] < 0) cls[k] = ncls++;
+  }
+  // coordinate descent: each pass visits the classes in turn and times every
+  // form of one class on the whole batch's steps, the other classes held at
+  // their current forms (so the overlap with them is part of the timing);
+  // the class keeps its form of the fastest time seen so far
+  std::vector<float> t((size_t)ncls * kBulkVariants, 0.f);
+  for (int r = 0; r < kTuneRounds; ++r)
+    for (int g = 0; g < ncls; ++g) {
+      for (int v = 0; v < kBulkVariants; ++v) {
+        for (int k = 0; k < n; ++k)
+          if (cls[k] == g) set_variant(b->ctxs[k], v);
+        if (vplbm_status st = vplbm_batch_step(b, kGraphMax)) return st;
+        float ms = 0.f;
+        if (vplbm_status st = timed(b->stream, trials, &ms,
+                                    [&] { return vplbm_batch_step(b, trials); }, nullptr))
+          return st;
+        float &tv = t[(size_t)g * kBulkVariants + v];
+        tv = r == 0 ? ms : std::min(tv, ms);
+      }
+      int best = 0;
+      for (int v = 1; v < kBulkVariants; ++v)
+        if (t[(size_t)g * kBulkVariants + v] < t[(size_t)g * kBulkVariants + best]) best = v;
+      for (int k = 0; k < n; ++k)
+        if (cls[k] == g) set_variant(b->ctxs[k], best);
+    }
+  if (variants)
+    for (int k = 0; k < n; ++k) variants[k] = b->ctxs[k]->bulk_variant;
   return VPLBM_OK;
 }
 

@@ -667,9 +667,9 @@ __device__ __forceinline__ bool update_node(const T (&h)[9], uint8_t m, int i, i
                                             T &pen_y) {
   pen_x = pen_y = (T)0;  // the penalization part of G (solid nodes only)
   if constexpr (kPacked) {
-    // 16-bit storage: the packed arithmetic of fluid_update, which the bulk
-    // kernels of these forms use, with the node in both lanes, so that a
-    // fluid node gets the same bits in either kernel
+    // FP32 compute (FP32 and 16-bit storage): the packed arithmetic of
+    // fluid_update, which the bulk kernels of these forms use, with the node
+    // in both lanes, so that a fluid node gets the same bits in either kernel
     F2 hv[9], ov[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) hv[a] = vsame(h[a]);
@@ -749,6 +749,52 @@ __device__ __forceinline__ bool update_node(const T (&h)[9], uint8_t m, int i, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// stochastic rounding of the stored populations (the _SR storage forms)
+// ---------------------------------------------------------------------------
+// hash of the level being written: the rounding counter, which the special
+// kernel advances by one per step
+__device__ __forceinline__ uint32_t sr_level(const StepArgs &p) {
+  const unsigned long long n = __ldg(p.rng_src);
+  return pcg_hash((uint32_t)n ^ (uint32_t)(n >> 32));
+}
+
+// The random bits of the node at linear index `node` for the nine values it
+// stores: three hashes and two exclusive-ors of them, five words whose 16-bit
+// halves are the populations' fields (population a: half a & 1 of word a / 2).
+// Any two of the five words are independent, so any two of the node's
+// roundings are uncorrelated.  Every kernel that stores the node draws the
+// same bits.
+struct SrBits {
+  uint32_t w[5];
+  __device__ __forceinline__ SrBits(uint32_t level, uint32_t node) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) w[q] = pcg_hash(level + node * 3u + (uint32_t)q);
+    w[3] = w[0] ^ w[1];
+    w[4] = w[1] ^ w[2];
+  }
+  // population a's field in the low half
+  __device__ __forceinline__ uint32_t lo(int a) const {
+    return (a & 1) ? w[a >> 1] >> 16 : w[a >> 1];
+  }
+  // population a's fields of this node (low half) and of node `up` (high half)
+  __device__ __forceinline__ uint32_t pair(const SrBits &up, int a) const {
+    return __byte_perm(w[a >> 1], up.w[a >> 1], (a & 1) ? 0x7632 : 0x5410);
+  }
+};
+
+// stores population value v of the node, rounded to the storage type (to
+// nearest, or stochastically with population a's bits)
+template <typename S, bool kSR>
+__device__ __forceinline__ void store_pop(S *ptr, typename Store<S>::T v, const SrBits *r, int a) {
+  if constexpr (sizeof(S) == 2 && kSR) {
+    *reinterpret_cast<unsigned short *>(ptr) =
+        (unsigned short)(Stochastic<S>::pair(v, v, r->lo(a)) & 0xffffu);
+  } else {
+    Store<S>::st(ptr, v);
+  }
+}
+
 // pre-collision populations of an edge node, with the side conditions
 template <typename S, bool kGather>
 __device__ __forceinline__ void edge_pops(const S *src, const typename Store<S>::T *prev,
@@ -796,10 +842,16 @@ __device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bo
     m = p.chi[node];
   }
   T o[9], pen_x, pen_y;
-  const bool bad = update_node<T, sizeof(S) == 2>(h, m, i, j, L, p.body_src, Consts<T>(p), o, pen_x,
+  const bool bad = update_node<T, sizeof(T) == 4>(h, m, i, j, L, p.body_src, Consts<T>(p), o, pen_x,
                                                   pen_y);
+  if (sizeof(S) == 2 && p.sr) {
+    const SrBits r(sr_level(p), (uint32_t)node);
 #pragma unroll
-  for (int a = 0; a < 9; ++a) Store<S>::st(dst + (int64_t)a * L.plane + node, o[a]);
+    for (int a = 0; a < 9; ++a) store_pop<S, true>(dst + (int64_t)a * L.plane + node, o[a], &r, a);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) store_pop<S, false>(dst + (int64_t)a * L.plane + node, o[a], nullptr, a);
+  }
   if (in_reg && (m & kInterface)) mem_terms<T>(p, o, i, j, m, tm, acc);
   if (in_reg && (m & kSolid)) {
     // volume integral (Eq. Angotforce, reading R19): the penalization force
@@ -817,11 +869,12 @@ __device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bo
 // special kernel: SIM blocks, then blocks of edge nodes, then the
 // force-region tiles (or, for the first step, every tile)
 // ---------------------------------------------------------------------------
-// With 16-bit storage the special kernels of lattices stepped side by side
-// share the SMs with a register-hungry bulk kernel: cap the special kernel at
-// 64 registers (four blocks per SM), which it meets without spilling.
+// The special kernels of lattices stepped side by side share the SMs with the
+// bulk kernels, whose bytes in flight need the register file: with FP32
+// compute the special kernel is capped at 64 registers (four blocks per SM),
+// at the price of a few spilled values.
 template <typename S>
-constexpr int kSpecialMinBlocks = sizeof(S) == 2 ? 4 : 1;
+constexpr int kSpecialMinBlocks = sizeof(S) <= 4 ? 4 : 1;
 
 template <typename S, bool kGather>
 __global__ void __launch_bounds__(kThreads, kSpecialMinBlocks<S>) special_kernel(const StepArgs p) {
@@ -832,6 +885,7 @@ __global__ void __launch_bounds__(kThreads, kSpecialMinBlocks<S>) special_kernel
   const int tid = threadIdx.y * kTileX + threadIdx.x;
   const ForceRegion reg = *p.reg_src;
   const int b = blockIdx.x;
+  if (p.sr && b == 0 && tid == 0) *p.rng_dst = *p.rng_src + 1ull;  // the next level's counter
   if (p.finalize_prev && b == (int)gridDim.x - 1) {
     // the previous step's force sums, beside this step's work
     finalize<T>(p, p.acc_prev);
@@ -964,6 +1018,70 @@ __global__ void __launch_bounds__(kThreads * kTiles) bulk_kernel(const StepArgs 
 }
 
 // ---------------------------------------------------------------------------
+// bulk kernel for FP32 storage: two adjacent nodes per thread, one 64-bit
+// load and one 64-bit store per plane, the +-x neighbour from the next lane by
+// a shuffle, and the collision of both nodes in packed f32x2 arithmetic (the
+// special kernel updates its fluid nodes with the same arithmetic, one node
+// in both lanes).  A tile row of 128 nodes is two warps; a block is kTiles
+// tiles high.
+// ---------------------------------------------------------------------------
+template <bool kForce, int kTiles>
+__global__ void __launch_bounds__(kThreads / 2 * kTiles) bulk32x2_kernel(const StepArgs p) {
+  const Lattice &L = p.L;
+  const int ti = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int i = ti * kTileX + 2 * threadIdx.x;  // the thread's nodes i, i + 1
+  const int j = blockIdx.y * (kTileY * kTiles) + threadIdx.y;
+  const int tj = j / kTileY;
+  // every lane loads from inside its row (clamped), so that the shuffles see
+  // all lanes; results of clamped lanes are never stored.  Rows start on
+  // 256-byte boundaries (the pitch is a multiple of 64 values).
+  const int ic = i < L.pitch - 2 ? i : L.pitch - 2;
+  const float *__restrict__ src = static_cast<const float *>(p.src);
+  F2 h[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    int r = j - cy_of(a);
+    r = r < 0 ? 0 : (r > L.ny - 1 ? L.ny - 1 : r);
+    const float *row = src + (int64_t)a * L.plane + (int64_t)r * L.pitch;
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(row + ic));
+    if (cx_of(a) == 0) {
+      h[a] = vpair(v.x, v.y);
+    } else if (cx_of(a) > 0) {  // sources i - 1 (the left lane's second value), i
+      float left = __shfl_up_sync(0xffffffffu, v.y, 1);
+      if (lane == 0) left = ic >= 1 ? __ldg(row + ic - 1) : 0.f;
+      h[a] = vpair(left, v.x);
+    } else {  // sources i + 1, i + 2 (the right lane's first value)
+      float right = __shfl_down_sync(0xffffffffu, v.x, 1);
+      if (lane == 31) right = ic + 2 < L.pitch ? __ldg(row + ic + 2) : 0.f;
+      h[a] = vpair(v.y, right);
+    }
+  }
+  {
+    const ForceRegion reg = *p.reg_src;
+    if (ti >= reg.ti0 && ti <= reg.ti1 && tj >= reg.tj0 && tj <= reg.tj1) return;  // special kernel
+  }
+  if (j < 1 || j > L.ny - 2) return;  // edge rows: special kernel
+  const bool ok0 = i >= 1 && i <= L.nx - 2, ok1 = i + 1 <= L.nx - 2;
+  if (!ok0 && !ok1) return;
+  F2 o[9];
+  const F2 rho = fluid_update<F2, kForce>(L, Consts<float>(p), h, o);
+  float *dst = static_cast<float *>(p.dst) + (int64_t)j * L.pitch + i;
+  if (ok0 && ok1) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a)
+      *reinterpret_cast<float2 *>(dst + (int64_t)a * L.plane) = make_float2(vlo(o[a]), vhi(o[a]));
+  } else {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      if (ok0) dst[(int64_t)a * L.plane] = vlo(o[a]);
+      if (ok1) dst[(int64_t)a * L.plane + 1] = vhi(o[a]);
+    }
+  }
+  if ((ok0 && rho_bad(vlo(rho))) || (ok1 && rho_bad(vhi(rho)))) atomicOr(p.status, kStatusUnstable);
+}
+
+// ---------------------------------------------------------------------------
 // bulk kernel for 16-bit storage: eight nodes per thread.  HBM stays busy
 // only with enough bytes in flight per SM, and a thread holds what it loads
 // in registers until it is used; with 2-byte values the registers, not the
@@ -1010,22 +1128,29 @@ __device__ __forceinline__ uint32_t shift16(uint32_t a, uint32_t b) {
 }
 
 // the update of the node pair whose pre-collision values are the packed
-// words w[a]; returns the packed post-collision words and rho
-template <typename S, bool kForce>
+// words w[a], nodes `node` and `node + 1`; returns the packed post-collision
+// words (rounded to nearest, or stochastically with the level's bits) and rho
+template <typename S, bool kForce, bool kSR>
 __device__ __forceinline__ F2 collide_pair16(const StepArgs &p, const uint32_t (&w)[9],
-                                             uint32_t (&out)[9]) {
+                                             uint32_t (&out)[9], uint32_t level, uint32_t node) {
   using P = Pair16<S>;
   F2 h[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) h[a] = vpair(P::lo(w[a]), P::hi(w[a]));
   F2 o[9];
   const F2 rho = fluid_update<F2, kForce>(p.L, Consts<float>(p), h, o);
+  if constexpr (kSR) {
+    const SrBits r0(level, node), r1(level, node + 1);
 #pragma unroll
-  for (int a = 0; a < 9; ++a) out[a] = P::pack(vlo(o[a]), vhi(o[a]));
+    for (int a = 0; a < 9; ++a) out[a] = Stochastic<S>::pair(vlo(o[a]), vhi(o[a]), r0.pair(r1, a));
+  } else {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) out[a] = P::pack(vlo(o[a]), vhi(o[a]));
+  }
   return rho;
 }
 
-template <typename S, bool kForce, int kMinBlocks>
+template <typename S, bool kForce, bool kSR, int kMinBlocks>
 __global__ void __launch_bounds__(32, kMinBlocks) bulk16_kernel(const StepArgs p) {
   const int ti = blockIdx.x, tj = blockIdx.y;
   const Lattice &L = p.L;
@@ -1079,9 +1204,11 @@ __global__ void __launch_bounds__(32, kMinBlocks) bulk16_kernel(const StepArgs p
   if (n_ok_hi < n_ok_lo) return;
   uint32_t out[4][9];
   bool bad = false;
+  const uint32_t level = kSR ? sr_level(p) : 0u;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const F2 r = collide_pair16<S, kForce>(p, w[k], out[k]);
+    const F2 r = collide_pair16<S, kForce, kSR>(p, w[k], out[k], level,
+                                           (uint32_t)((int64_t)j * L.pitch + i + 2 * k));
     bad |= (2 * k >= n_ok_lo && 2 * k <= n_ok_hi && rho_bad(vlo(r))) ||
            (2 * k + 1 >= n_ok_lo && 2 * k + 1 <= n_ok_hi && rho_bad(vhi(r)));
   }
@@ -1106,7 +1233,7 @@ __global__ void __launch_bounds__(32, kMinBlocks) bulk16_kernel(const StepArgs p
 
 // The same update with four nodes per thread (one 64-bit load per plane, one
 // warp per tile row, 80 registers): a variant for the tuner.
-template <typename S, bool kForce>
+template <typename S, bool kForce, bool kSR>
 __global__ void __launch_bounds__(32 * kTileY, 12) bulk16x4_kernel(const StepArgs p) {
   const int ti = blockIdx.x, tj = blockIdx.y;
   const Lattice &L = p.L;
@@ -1156,10 +1283,12 @@ __global__ void __launch_bounds__(32 * kTileY, 12) bulk16x4_kernel(const StepArg
   S *dst = static_cast<S *>(p.dst) + (int64_t)j * L.pitch + i;
   // the two pairs one after the other, each stored as soon as it is done
   bool bad = false;
+  const uint32_t level = kSR ? sr_level(p) : 0u;
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     uint32_t o[9];
-    const F2 r = collide_pair16<S, kForce>(p, half ? wb : wa, o);
+    const F2 r = collide_pair16<S, kForce, kSR>(p, half ? wb : wa, o, level,
+                                           (uint32_t)((int64_t)j * L.pitch + i + 2 * half));
     const bool ok0 = ok[2 * half], ok1 = ok[2 * half + 1];
     S *d2 = dst + 2 * half;
     if (ok0 && ok1) {
@@ -1207,17 +1336,30 @@ __global__ void __launch_bounds__(kThreads) mask_kernel(const StepArgs p) {
     p.chi[(int64_t)j * p.L.pitch + i] = tile_mask_byte(p.L, tm, i, j, threadIdx.x, threadIdx.y);
 }
 
+template <typename S, bool kForce, bool kSR>
+cudaError_t bulk16_v(int variant, const StepArgs &a, cudaStream_t s) {
+  static_assert(kTileX == 8 * 16 && kTileY == 2, "bulk16_kernel maps a tile onto one warp");
+  const dim3 grid(a.ntiles_x, a.ntiles_y);
+  switch (variant) {
+    case 0: bulk16_kernel<S, kForce, kSR, 20><<<grid, dim3(32), 0, s>>>(a); break;  // 8 nodes, 96 regs
+    case 1: bulk16_kernel<S, kForce, kSR, 16><<<grid, dim3(32), 0, s>>>(a); break;  // 8 nodes, 126 regs
+    case 2: bulk16x4_kernel<S, kForce, kSR><<<grid, dim3(32, kTileY), 0, s>>>(a); break;  // 4 nodes
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 template <typename S, bool kForce>
 cudaError_t bulk_v(int variant, const StepArgs &a, cudaStream_t s) {
   if constexpr (sizeof(S) == 2) {
-    static_assert(kTileX == 8 * 16 && kTileY == 2, "bulk16_kernel maps a tile onto one warp");
-    const dim3 grid(a.ntiles_x, a.ntiles_y);
-    switch (variant) {
-      case 0: bulk16_kernel<S, kForce, 20><<<grid, dim3(32), 0, s>>>(a); break;  // 8 nodes, 96 regs
-      case 1: bulk16_kernel<S, kForce, 16><<<grid, dim3(32), 0, s>>>(a); break;  // 8 nodes, 126 regs
-      case 2: bulk16x4_kernel<S, kForce><<<grid, dim3(32, kTileY), 0, s>>>(a); break;  // 4 nodes
-      default: return cudaErrorInvalidValue;
-    }
+    return a.sr ? bulk16_v<S, kForce, true>(variant, a, s) : bulk16_v<S, kForce, false>(variant, a, s);
+  } else if constexpr (sizeof(S) == 4) {
+    const int k = variant == 0 ? 1 : (variant == 1 ? 2 : 4);  // tiles per block
+    if (variant < 0 || variant > 2) return cudaErrorInvalidValue;
+    const dim3 grid(a.ntiles_x, (a.ntiles_y + k - 1) / k), block(kTileX / 2, kTileY * k);
+    if (k == 1) bulk32x2_kernel<kForce, 1><<<grid, block, 0, s>>>(a);
+    else if (k == 2) bulk32x2_kernel<kForce, 2><<<grid, block, 0, s>>>(a);
+    else bulk32x2_kernel<kForce, 4><<<grid, block, 0, s>>>(a);
   } else {
     const int k = variant == 0 ? 1 : (variant == 1 ? 2 : 4);  // tiles per block
     if (variant < 0 || variant > 2) return cudaErrorInvalidValue;

@@ -449,7 +449,60 @@ struct StepArgs {
   int32_t raster;           // 1 (a moving body): the force-region tiles rasterise chi
                             // from body_src themselves, and SIM tests nodes with the
                             // predicate instead of reading chi
+  int32_t sr;               // 1: 16-bit stores round stochastically
+  const unsigned long long *rng_src;  // the rounding counter of this step's level
+  unsigned long long *rng_dst;        // ... and of the next (written by the special kernel)
 };
+
+// storage type of a dtype's populations, for the kernels' dispatch: the
+// stochastically rounded forms store FP16 / BF16 like the nearest-rounded ones
+__host__ __device__ inline int storage_dtype(int dtype) {
+  return dtype == VPLBM_F16_SR ? VPLBM_F16_OFS : (dtype == VPLBM_BF16_SR ? VPLBM_BF16_OFS : dtype);
+}
+__host__ __device__ inline bool stochastic_dtype(int dtype) {
+  return dtype == VPLBM_F16_SR || dtype == VPLBM_BF16_SR;
+}
+
+// ---------------------------------------------------------------------------
+// stochastic rounding to 16 bits
+// ---------------------------------------------------------------------------
+// 32-bit hash of a 32-bit input: the "PCG hash" of Jarzynski and Olano, Hash
+// Functions for GPU Rendering, JCGT 9(3), 2020 (one step of a PCG generator
+// with an RXS-M-XS output permutation).
+__host__ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
+  const uint32_t state = v * 747796405u + 2891336453u;
+  const uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+  return (word >> 22u) ^ word;
+}
+
+// Stochastic rounding by the conversion instruction of sm_100 and later
+// (cvt.rs): a pair of FP32 values to a packed pair of 16-bit values, each
+// rounded to one of its two neighbours in the format, away from zero with
+// probability (distance from the one toward zero) / (their spacing).  The
+// instruction adds random bits just below the kept ones and truncates; the
+// lower element takes bits 0..12 (FP16) or 0..15 (BF16) of rbits, the upper
+// element bits 16..28 or 16..31.  With all of the value's dropped bits covered
+// by the random ones (13 for FP16 in its normal range, 16 for BF16) the
+// rounding is exactly unbiased.
+template <typename S>
+struct Stochastic;
+template <>
+struct Stochastic<__half> {
+  static __device__ __forceinline__ uint32_t pair(float lo, float hi, uint32_t rbits) {
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+  }
+};
+template <>
+struct Stochastic<__nv_bfloat16> {
+  static __device__ __forceinline__ uint32_t pair(float lo, float hi, uint32_t rbits) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+  }
+};
+
 
 // the nodes on the lattice edges, enumerated: first row, last row, then the
 // first and the last column between them

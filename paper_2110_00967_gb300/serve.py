@@ -176,7 +176,7 @@ class GpuBackend:
     """Lattices of the CUDA library for NACA 0012 requests (geometry scaled
     with nx, Re 1000, inlet u = 0.05), in the given storage form."""
 
-    def __init__(self, dtype: str = "f32", device=None):
+    def __init__(self, dtype: str = "f32", device=None, tune_trials: int = 0):
         import torch
         from . import vplbm as V
         from . import workloads as W
@@ -184,6 +184,10 @@ class GpuBackend:
         self.dtype = dtype
         self.device = torch.device(device if device is not None else "cuda")
         self.stream = torch.cuda.current_stream(self.device)
+        # launch form of the bulk kernel per grid size, tuned once per size on
+        # a scratch lattice (tune_trials > 0) or the default form (0)
+        self.tune_trials = tune_trials
+        self.forms: dict = {}
 
     def workload(self, req):
         return self.W.naca(req.alpha_deg, dtype=self.dtype, nx=req.nx, ny=req.ny)
@@ -191,10 +195,23 @@ class GpuBackend:
     def nbytes(self, req) -> int:
         return self.V.vplbm_workspace_bytes(self.V.config_of(self.workload(req))) + 256
 
+    def form(self, w) -> int:
+        """The launch form for the workload's grid size: the tuner's choice on
+        a scratch lattice of that size (its steps touch no request)."""
+        key = (w.nx, w.ny)
+        if key not in self.forms:
+            scratch = self.V.Lattice(self.V.config_of(w), device=self.device, stream=self.stream)
+            scratch.set_body(self.V.body_of(w))
+            self.forms[key] = scratch.autotune(self.tune_trials)
+            scratch.close()
+        return self.forms[key]
+
     def make(self, req):
         w = self.workload(req)
         lat = self.V.Lattice(self.V.config_of(w), device=self.device, stream=self.stream)
         lat.set_body(self.V.body_of(w))
+        if self.tune_trials > 0:
+            lat.bulk_variant = self.form(w)
         lat.reset_sums()
         return lat
 

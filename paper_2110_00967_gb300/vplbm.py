@@ -16,7 +16,7 @@ from . import build as _build
 
 # enums (values of include/vplbm.h)
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
-F64, F32, F16_OFS, BF16_OFS = range(4)
+F64, F32, F16_OFS, BF16_OFS, F16_SR, BF16_SR = range(6)
 BGK, TRT = 0, 1
 FORCING_PAPER, FORCING_SPLIT = 0, 1
 PERIODIC, INLET_BB, OUTLET_CONVECTIVE, SYMMETRY, NOSLIP_BB, OUTLET_FREE = range(6)
@@ -359,10 +359,11 @@ def vplbm_batch_prepare(batch, nsteps: int):
     _check(lib().vplbm_batch_prepare(batch, nsteps))
 
 
-def vplbm_batch_autotune(batch, trials: int = 20) -> int:
-    v = C.c_int32()
-    _check(lib().vplbm_batch_autotune(batch, trials, C.byref(v)))
-    return v.value
+def vplbm_batch_autotune(batch, n: int, trials: int = 20) -> list:
+    """Per-lattice launch forms chosen by the batch tuner (n lattices)."""
+    v = (C.c_int32 * n)()
+    _check(lib().vplbm_batch_autotune(batch, trials, v))
+    return list(v)
 
 
 def vplbm_batch_destroy(batch):
@@ -521,7 +522,8 @@ class Lattice:
 # ---------------------------------------------------------------------------
 # workloads -> ABI structures
 # ---------------------------------------------------------------------------
-_DTYPES = {"f64": F64, "f32": F32, "f16": F16_OFS, "bf16": BF16_OFS}
+_DTYPES = {"f64": F64, "f32": F32, "f16": F16_OFS, "bf16": BF16_OFS, "f16sr": F16_SR,
+           "bf16sr": BF16_SR}
 _BCS = {"periodic": PERIODIC, "inlet": INLET_BB, "outlet": OUTLET_CONVECTIVE,
         "symmetry": SYMMETRY, "noslip": NOSLIP_BB, "outlet_free": OUTLET_FREE}
 _KINDS = {"none": BODY_NONE, "disk": BODY_DISK, "naca": BODY_NACA4}
@@ -571,8 +573,9 @@ class Batch:
     def prepare(self, n: int):
         vplbm_batch_prepare(self.handle, n)
 
-    def autotune(self, trials: int = 20) -> int:
-        return vplbm_batch_autotune(self.handle, trials)
+    def autotune(self, trials: int = 20) -> list:
+        """Each member's launch form, tuned per size class."""
+        return vplbm_batch_autotune(self.handle, len(self.lattices), trials)
 
     @property
     def launches(self) -> int:

@@ -48,7 +48,7 @@ class Workload:
     name: str
     nx: int
     ny: int
-    dtype: str  # "f64" | "f32" | "f16" | "bf16"
+    dtype: str  # "f64" | "f32" | "f16" | "bf16" | "f16sr" | "bf16sr" (stochastic rounding)
     collision: str  # "bgk" | "trt"
     tau_plus: float
     u_in: tuple

@@ -47,4 +47,4 @@ def test_configuration_block():
     assert c32["storage"] == "f32" and "offsets" in c16["storage"]
     assert "range replay" in c32["l2"] and "range replay" not in c16["l2"]
     assert c32["grid"] == [2048, 1024] and c32["instances"] == 5
-    assert bench.BYTES_PER_LUP == {"f32": 72, "f16": 36, "bf16": 36}
+    assert bench.BYTES_PER_LUP == {"f32": 72, "f16": 36, "bf16": 36, "f16sr": 36, "bf16sr": 36}

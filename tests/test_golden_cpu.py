@@ -54,3 +54,46 @@ def test_serving_subset_is_the_seeded_mix():
         assert r.alpha_deg == g["alpha_deg"]
         assert g["cd_mem"] > 0 and g["cd_sim"] > 0
         assert g["cl_mem"] * g["alpha_deg"] >= 0  # lift follows the incidence
+
+
+def test_stochastic_storage_envelopes_are_ordered_by_format():
+    """Stochastic rounding to a format moves the oracle by the same order as
+    rounding to nearest in that format: FP16 (unit 2^-11) well below BF16
+    (2^-8), and both far above FP32."""
+    d = load("storage_envelopes.json")
+    for case in ("naca0-512", "naca10-512"):
+        for offs in ("free-stream", "weights"):
+            c = {f: d["cases"][f"{case}/{offs}/{f}"] for f in ("f32", "f16", "f16sr", "bf16sr")}
+            u = {f: max(v["fields"][1:]) for f, v in c.items()}
+            assert u["f32"] < u["f16sr"] < u["bf16sr"]
+            assert 0.25 * u["f16"] <= u["f16sr"] <= 4 * u["f16"]
+
+
+def test_sedimentation_trajectory_is_a_settling_fall():
+    """The stored trajectories of the disk in the closed box: it starts from
+    rest and falls (v < 0 along y) ever faster over the first samples, never
+    faster than free fall with buoyancy and no drag, ((1 - 1/rho_r) g t);
+    the fluid force opposes the fall (F_y > 0); the positions are the
+    trapezoid integral of the sampled velocities; MEM and SIM, two estimates
+    of the same force, give fall displacements within 5 % of each other."""
+    from paper_2110_00967_gb300 import workloads as W
+    d = load("sedimentation_trajectory.json")
+    every = d["every"]
+    falls = {}
+    for est, c in d["cases"].items():
+        w = W.sedimentation(est)
+        b, f = np.array(c["body"]), np.array(c["force"])
+        g = w.body.gravity[1]
+        t = every * np.arange(1, len(b) + 1)
+        v = b[:, 4]
+        assert np.all(v < 0) and np.all(np.diff(v[:10]) < 0)
+        assert np.all(np.abs(v) < (1 - 1 / w.body.density_ratio) * abs(g) * t)
+        assert np.all(f[5:, 1] > 0)
+        # y(t_k) - y0 against the trapezoid integral of v through the samples
+        # (v = 0 at t = 0); the sampling error is far below 1 % of the fall
+        y = b[:, 1] - w.body.y_c
+        integral = np.concatenate(([0.5 * every * v[0]],
+                                   0.5 * every * v[0] + np.cumsum(0.5 * every * (v[1:] + v[:-1]))))
+        assert np.all(np.abs(y[10:] - integral[10:]) <= 0.01 * np.abs(y[10:]))
+        falls[est] = -y[-1]
+    assert abs(falls["mem"] - falls["sim"]) <= 0.05 * falls["mem"]

@@ -45,6 +45,8 @@ def assert_same(a, b):
 CASES = {
     "naca-f16": lambda: W.naca(12.0, dtype="f16", nx=512, ny=256),
     "naca-f32": lambda: W.naca(12.0, dtype="f32", nx=512, ny=256),
+    # stochastic rounding: the snapshot carries the rounding counter
+    "naca-f16sr": lambda: W.naca(12.0, dtype="f16sr", nx=512, ny=256),
     # a disk of the sedimentation box's proportions falling in a closed box,
     # rigid body driven by SIM; chi re-rasterised every step
     "fall-f32": lambda: W.Workload(

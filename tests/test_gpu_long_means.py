@@ -76,3 +76,26 @@ def test_fp32_time_means_within_1e3_of_the_oracle():
         print("f32", a, {k: f"{got[a][k]:.5f} ({err[a][k]:.1e})" for k in KEYS})
     worst = max(max(e.values()) for e in err.values())
     assert worst <= 1e-3, err
+
+
+def test_f16_stochastic_time_means_within_1e3_of_the_oracle():
+    """FP16 offsets rounded stochastically when stored (the f16sr form): every
+    mean coefficient within 1e-3 of the oracle's, but for the lift at zero
+    incidence.  There the oracle's lift vanishes by the airfoil's mirror
+    symmetry, which the per-node random rounding does not keep: the served
+    lift is the mean of that rounding's noise, and it is held to 1e-3 in
+    absolute terms (|Cl - Cl_oracle| <= 1e-3) instead of relative to the 1e-2
+    floor.  FP16 rounded to nearest misses the 1e-3 bar at every angle (its
+    rounding error does not average out over the window), which is why the
+    stochastic form exists."""
+    ref, got = gpu_means("f16sr")
+    err = errors(ref, got)
+    for a in err:
+        print("f16sr", a, {k: f"{got[a][k]:.5f} ({err[a][k]:.1e})" for k in KEYS})
+    for a, e in err.items():
+        for k in KEYS:
+            if a == 0.0 and k.startswith("cl"):
+                r = ref["angles"][f"{a:g}"][k]
+                assert abs(got[a][k] - r) <= 1e-3, (a, k, got[a][k], r)
+            else:
+                assert e[k] <= 1e-3, (a, k, e[k])

@@ -36,7 +36,7 @@ def ragged_naca(dtype, body_force=(0.0, 0.0)):
     return w.with_(body_force=body_force)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16", "bf16", "f16sr", "bf16sr"])
 @pytest.mark.parametrize("force", [False, True])
 def test_every_form_gives_the_same_populations(dtype, force):
     w = ragged_naca(dtype, body_force=(1e-6, -2e-6) if force else (0.0, 0.0))
@@ -94,12 +94,32 @@ def test_batch_tuner_steps_are_ordinary_steps():
     batch = V.Batch(lats)
     batch.step(10)
     v = batch.autotune(2)
-    assert 0 <= v < N_VARIANTS and all(l.bulk_variant == v for l in lats)
+    assert len(v) == 3 and len(set(v)) == 1 and 0 <= v[0] < N_VARIANTS
+    assert all(l.bulk_variant == v[0] for l in lats)
     batch.step(20)
     batch.close()
     plain = lattice(w)
     plain.step(30 + tuning_steps(2))
     for l in lats:
+        assert np.array_equal(l.get_f(), plain.get_f())
+
+
+def test_batch_tuner_picks_a_form_per_size_class():
+    """Members of one size and storage type share a form; two classes give
+    each lattice 2 * 9 * (32 + trials) tuning steps, ordinary steps again."""
+    works = [W.naca(5.0, dtype="f16", nx=384, ny=192), W.naca(12.0, dtype="f32", nx=256, ny=128),
+             W.naca(7.0, dtype="f16", nx=384, ny=192)]
+    lats = [lattice(w) for w in works]
+    batch = V.Batch(lats)
+    v = batch.autotune(2)
+    assert v[0] == v[2] and all(0 <= x < N_VARIANTS for x in v)
+    assert [l.bulk_variant for l in lats] == v
+    batch.step(5)
+    batch.close()
+    for w, l in zip(works, lats):
+        plain = lattice(w)
+        plain.step(5 + 2 * tuning_steps(2))
+        assert l.steps == plain.steps
         assert np.array_equal(l.get_f(), plain.get_f())
 
 
@@ -119,7 +139,7 @@ def test_tuner_rejects_bad_input():
     assert e.value.status == V.EINVAL
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16", "f16sr", "bf16sr"])
 @pytest.mark.parametrize("force", [False, True])
 def test_bulk_and_special_kernels_update_a_node_alike(dtype, force):
     """A fluid node gets the same bits from the bulk kernel (any launch form)
@@ -141,3 +161,51 @@ def test_bulk_and_special_kernels_update_a_node_alike(dtype, force):
         pulled.step(1)
         inplace.step(1)
         assert np.array_equal(pulled.get_f(), inplace.get_f()), f"form {v}"
+
+
+@pytest.mark.parametrize("dtype", ["f16sr", "bf16sr"])
+def test_stochastic_rounding_is_reproducible_and_unbiased(dtype):
+    """The stochastically rounded storage forms: two runs of the same lattice
+    are bit-identical (the rounding bits come from a hash of the step count,
+    node and population), they differ from rounding to nearest, and each
+    stored value is one of the two 16-bit neighbours of the value rounding to
+    nearest would store, at most one unit apart."""
+    w = ragged_naca(dtype)
+    a, b = lattice(w), lattice(w)
+    rne = lattice(w.with_(dtype=dtype[:-2]))
+    for lat in (a, b, rne):
+        lat.step(40)
+    fa, fb, fr = a.get_f(), b.get_f(), rne.get_f()
+    assert np.array_equal(fa, fb)
+    assert not np.array_equal(fa, fr)
+    # one step from the same state: SR and RNE stores are neighbours
+    st = a.get_f()
+    for lat in (a, rne):
+        lat.set_state(st, post_collision=False)
+        lat.step(1)
+    E = lat_E(w)
+    ha, hr = a.get_f() - E, rne.get_f() - E
+    # the larger of the two gaps next to the nearest value (at a power of two
+    # the stochastic choice may be the neighbour in the larger binade)
+    if dtype.startswith("f16"):
+        h16 = hr.astype(np.float16)
+        spacing = np.maximum(
+            np.abs(np.nextafter(h16, np.float16(np.inf)).astype(np.float64) - hr),
+            np.abs(np.nextafter(h16, np.float16(-np.inf)).astype(np.float64) - hr))
+    else:
+        m, e = np.frexp(hr)
+        spacing = np.ldexp(1.0 / 256.0, e)
+    # (f - E in FP64 carries up to an FP64 unit of E, about 1e-16)
+    assert np.all(np.abs(ha - hr) <= spacing * (1 + 1e-6) + 1e-15)
+    frac_diff = np.mean(ha != hr)
+    assert 0.01 < frac_diff < 0.99, frac_diff
+
+
+def lat_E(w):
+    """E_a = feq_a(1, u_ref) of the workload, broadcast over the lattice."""
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    wt = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    ux, uy = (float(np.float32(v)) for v in w.u_ref)
+    cu = cx * ux + cy * uy
+    return (wt * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy)))[:, None, None]
