@@ -47,6 +47,10 @@ STORAGE_NAME = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16", "f16sr
 DTYPE_NAME = {"f32": "f32", "f16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute",
               "f16sr": "f16-storage-stochastic/f32-compute",
               "bf16sr": "bf16-storage-stochastic/f32-compute"}
+# the bulk kernel of each storage form (the special kernel runs beside it)
+BULK_NAME = {"f32": "bulk32x2_kernel", "f16": "bulk16_kernel<__half>",
+             "bf16": "bulk16_kernel<__nv_bfloat16>", "f16sr": "bulk16_kernel<__half, sr>",
+             "bf16sr": "bulk16_kernel<__nv_bfloat16, sr>"}
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_naca2048_f32.md")
 KERNEL_SOURCES = ("paper_2110_00967_gb300/csrc/step.cu",
                   "paper_2110_00967_gb300/csrc/vplbm_internal.cuh",
@@ -65,7 +69,7 @@ def config_block(dtype: str = "f32", extra=None):
          "storage": "f32" if dtype == "f32" else f"{dtype} offsets from feq(1, u_in)",
          "forces_per_step": ["mem", "sim-849"],
          "l2": f"inputs larger than L2: 5 lattices x {mb} MB ping-pong, stepped side by side"
-               + (" (ncu range replay: DRAM traffic 154.0 MB per lattice step, 151.0 algorithmic)"
+               + (" (ncu range replay: DRAM traffic 154.7 MB per lattice step, 151.0 algorithmic)"
                   if dtype == "f32" else "")}
     if extra:
         c.update(extra)
@@ -323,7 +327,7 @@ def run_ours(args, rank, world, local_rank):
                                             "bulk_variant": variants}),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": f"one lattice step: bulk_kernel<{STORAGE_NAME[args.dtype]}> with "
+                     "kernel": f"one lattice step: {BULK_NAME[args.dtype]} with "
                                f"special_kernel<{STORAGE_NAME[args.dtype]}> beside it, timed over "
                                "the region",
                      "kernel_avg_us": round(lattice_step_ms * 1e3, 3),
@@ -462,6 +466,14 @@ def run_serving(args, rank, world, local_rank):
     mean_nodes = sum(nx * ny for nx, ny in W.SERVING_GRIDS) / len(W.SERVING_GRIDS)
     solve_s = t_cal * mean_nodes / (1024 * 512)
     rate = 4.0 / solve_s
+    # launch forms per grid size, tuned once at server start (outside the
+    # served time): together in one batch of the mix's sizes, or each size
+    # alone when it first arrives
+    t = time.perf_counter()
+    if args.tune_trials > 0 and args.tune_mode == "mix":
+        backend.tune_mix(W.SERVING_GRIDS)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t
     reqs = W.serving_requests(args.requests, rate=rate)
     srv = S.Server(backend, memory_bytes=args.memory_gb << 30, window=1000, tol=1e-4,
                    cap=args.cap, max_active=args.max_active)
@@ -490,6 +502,11 @@ def run_serving(args, rank, world, local_rank):
                    "max_active": args.max_active or "memory-bound",
                    "bulk_forms": ({f"{k[0]}x{k[1]}": v for k, v in sorted(backend.forms.items())}
                                   if args.tune_trials else "default"),
+                   "tuning": (f"{args.tune_mode}, {args.tune_trials} timed steps per form, "
+                              f"{tune_s:.2f} s at server start" if args.tune_trials and
+                              args.tune_mode == "mix" else
+                              f"{args.tune_mode}, {args.tune_trials} timed steps per form, "
+                              "inside the served time" if args.tune_trials else "none"),
                    "parallelism": f"replicas{world}"},
         "p50_s": round(summ["p50_s"], 4), "p99_s": round(summ["p99_s"], 4),
         "latency": "arrival to converged Cd/Cl, converged requests only",
@@ -775,8 +792,12 @@ def main(argv=None):
     ap.add_argument("--cap", type=int, default=200000, help="serving: step cap per request")
     ap.add_argument("--memory-gb", type=int, default=40, help="serving: device-memory budget")
     ap.add_argument("--tune-trials", type=int, default=16,
-                    help="serving: timed steps per launch form when a grid size is first "
-                         "seen (0: the default form everywhere)")
+                    help="serving: timed steps per launch form in the tuner (0: the default "
+                         "form everywhere)")
+    ap.add_argument("--tune-mode", choices=("mix", "alone"), default="mix",
+                    help="serving: tune the launch forms of the mix's grid sizes together in "
+                         "one batch at server start (mix), or each size alone on a scratch "
+                         "lattice when it first arrives (alone)")
     ap.add_argument("--max-active", type=int, default=0,
                     help="serving: most requests stepped at once (0: as many as fit; 1: one "
                          "request at a time, the single-instance comparison)")

@@ -759,37 +759,44 @@ __device__ __forceinline__ uint32_t sr_level(const StepArgs &p) {
   return pcg_hash((uint32_t)n ^ (uint32_t)(n >> 32));
 }
 
-// The random bits of the node at linear index `node` for the nine values it
-// stores: three hashes and two exclusive-ors of them, five words whose 16-bit
-// halves are the populations' fields (population a: half a & 1 of word a / 2).
-// Any two of the five words are independent, so any two of the node's
-// roundings are uncorrelated.  Every kernel that stores the node draws the
-// same bits.
+// The random bits of a node pair (the nodes 2q and 2q + 1 of the linear index
+// j * pitch + i; a row starts at an even index, the pitch being a multiple of
+// 64) for the eighteen values it stores: four hashes, and nine words made of
+// distinct exclusive-ors of them, one word per population.  The low half of
+// population a's word serves the even node, the high half the odd one (the
+// lanes of the conversion).  Distinct subsets of independent uniform words
+// are pairwise independent, so any two roundings of the pair are
+// uncorrelated.  Every kernel that stores a node draws the same bits.
 struct SrBits {
-  uint32_t w[5];
-  __device__ __forceinline__ SrBits(uint32_t level, uint32_t node) {
+  uint32_t h[4];
+  __device__ __forceinline__ SrBits(uint32_t level, uint32_t pair) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) w[q] = pcg_hash(level + node * 3u + (uint32_t)q);
-    w[3] = w[0] ^ w[1];
-    w[4] = w[1] ^ w[2];
+    for (int q = 0; q < 4; ++q) h[q] = pcg_hash(level + pair * 4u + (uint32_t)q);
   }
-  // population a's field in the low half
-  __device__ __forceinline__ uint32_t lo(int a) const {
-    return (a & 1) ? w[a >> 1] >> 16 : w[a >> 1];
-  }
-  // population a's fields of this node (low half) and of node `up` (high half)
-  __device__ __forceinline__ uint32_t pair(const SrBits &up, int a) const {
-    return __byte_perm(w[a >> 1], up.w[a >> 1], (a & 1) ? 0x7632 : 0x5410);
+  __device__ __forceinline__ uint32_t word(int a) const {
+    switch (a) {
+      case 0: return h[0];
+      case 1: return h[1];
+      case 2: return h[2];
+      case 3: return h[3];
+      case 4: return h[0] ^ h[1];
+      case 5: return h[2] ^ h[3];
+      case 6: return h[0] ^ h[2];
+      case 7: return h[1] ^ h[3];
+      default: return h[0] ^ h[3];
+    }
   }
 };
 
-// stores population value v of the node, rounded to the storage type (to
-// nearest, or stochastically with population a's bits)
+// stores population value v of node `node`, rounded to the storage type (to
+// nearest, or stochastically with the bits of the node's pair)
 template <typename S, bool kSR>
-__device__ __forceinline__ void store_pop(S *ptr, typename Store<S>::T v, const SrBits *r, int a) {
+__device__ __forceinline__ void store_pop(S *ptr, typename Store<S>::T v, const SrBits *r, int a,
+                                          uint32_t node) {
   if constexpr (sizeof(S) == 2 && kSR) {
+    const uint32_t w = r->word(a);
     *reinterpret_cast<unsigned short *>(ptr) =
-        (unsigned short)(Stochastic<S>::pair(v, v, r->lo(a)) & 0xffffu);
+        (unsigned short)(Stochastic<S>::pair(v, v, (node & 1u) ? w >> 16 : w) & 0xffffu);
   } else {
     Store<S>::st(ptr, v);
   }
@@ -845,12 +852,14 @@ __device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bo
   const bool bad = update_node<T, sizeof(T) == 4>(h, m, i, j, L, p.body_src, Consts<T>(p), o, pen_x,
                                                   pen_y);
   if (sizeof(S) == 2 && p.sr) {
-    const SrBits r(sr_level(p), (uint32_t)node);
+    const SrBits r(sr_level(p), (uint32_t)node >> 1);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) store_pop<S, true>(dst + (int64_t)a * L.plane + node, o[a], &r, a);
+    for (int a = 0; a < 9; ++a)
+      store_pop<S, true>(dst + (int64_t)a * L.plane + node, o[a], &r, a, (uint32_t)node);
   } else {
 #pragma unroll
-    for (int a = 0; a < 9; ++a) store_pop<S, false>(dst + (int64_t)a * L.plane + node, o[a], nullptr, a);
+    for (int a = 0; a < 9; ++a)
+      store_pop<S, false>(dst + (int64_t)a * L.plane + node, o[a], nullptr, a, (uint32_t)node);
   }
   if (in_reg && (m & kInterface)) mem_terms<T>(p, o, i, j, m, tm, acc);
   if (in_reg && (m & kSolid)) {
@@ -870,14 +879,16 @@ __device__ __forceinline__ bool special_node(const StepArgs &p, int i, int j, bo
 // force-region tiles (or, for the first step, every tile)
 // ---------------------------------------------------------------------------
 // The special kernels of lattices stepped side by side share the SMs with the
-// bulk kernels, whose bytes in flight need the register file: with FP32
-// compute the special kernel is capped at 64 registers (four blocks per SM),
-// at the price of a few spilled values.
+// bulk kernels, whose bytes in flight need the register file: for a fixed
+// body with FP32 compute the special kernel is capped at 64 registers (four
+// blocks per SM), at the price of a few spilled values.  A moving body's
+// special kernel is on the step's critical path (its force feeds the next
+// step), so it keeps all the registers it wants (kMinBlocks 1).
 template <typename S>
 constexpr int kSpecialMinBlocks = sizeof(S) <= 4 ? 4 : 1;
 
-template <typename S, bool kGather>
-__global__ void __launch_bounds__(kThreads, kSpecialMinBlocks<S>) special_kernel(const StepArgs p) {
+template <typename S, bool kGather, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) special_kernel(const StepArgs p) {
   using T = typename Store<S>::T;
   __shared__ int is_last;
   __shared__ TileMask tmask;
@@ -1140,9 +1151,9 @@ __device__ __forceinline__ F2 collide_pair16(const StepArgs &p, const uint32_t (
   F2 o[9];
   const F2 rho = fluid_update<F2, kForce>(p.L, Consts<float>(p), h, o);
   if constexpr (kSR) {
-    const SrBits r0(level, node), r1(level, node + 1);
+    const SrBits r(level, node >> 1);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) out[a] = Stochastic<S>::pair(vlo(o[a]), vhi(o[a]), r0.pair(r1, a));
+    for (int a = 0; a < 9; ++a) out[a] = Stochastic<S>::pair(vlo(o[a]), vhi(o[a]), r.word(a));
   } else {
 #pragma unroll
     for (int a = 0; a < 9; ++a) out[a] = P::pack(vlo(o[a]), vhi(o[a]));
@@ -1310,8 +1321,11 @@ __global__ void __launch_bounds__(32 * kTileY, 12) bulk16x4_kernel(const StepArg
 template <typename S, bool kGather>
 cudaError_t special_t(const StepArgs &a, cudaStream_t s) {
   const int tiles = a.all_tiles ? a.ntiles_x * a.ntiles_y : a.edge_blocks + a.region_slots;
-  special_kernel<S, kGather>
-      <<<a.sim_blocks + tiles + (a.finalize_prev ? 1 : 0), dim3(kTileX, kTileY), 0, s>>>(a);
+  const int blocks = a.sim_blocks + tiles + (a.finalize_prev ? 1 : 0);
+  if (a.raster || kSpecialMinBlocks<S> == 1)
+    special_kernel<S, kGather, 1><<<blocks, dim3(kTileX, kTileY), 0, s>>>(a);
+  else
+    special_kernel<S, kGather, kSpecialMinBlocks<S>><<<blocks, dim3(kTileX, kTileY), 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -184,8 +184,9 @@ class GpuBackend:
         self.dtype = dtype
         self.device = torch.device(device if device is not None else "cuda")
         self.stream = torch.cuda.current_stream(self.device)
-        # launch form of the bulk kernel per grid size, tuned once per size on
-        # a scratch lattice (tune_trials > 0) or the default form (0)
+        # launch form of the bulk kernel per grid size: the default form
+        # (tune_trials 0), or tuned (tune_mix, or once per size on a scratch
+        # lattice when a size first arrives)
         self.tune_trials = tune_trials
         self.forms: dict = {}
 
@@ -194,6 +195,25 @@ class GpuBackend:
 
     def nbytes(self, req) -> int:
         return self.V.vplbm_workspace_bytes(self.V.config_of(self.workload(req))) + 256
+
+    def tune_mix(self, grids, alpha_deg: float = 10.0) -> dict:
+        """Launch forms for the given grid sizes, tuned together: one scratch
+        lattice per size stepped as one batch, the batch tuner choosing a
+        form per size with the other sizes running beside it, as they do
+        when served.  The choices are kept for the requests to come."""
+        lats = []
+        for nx, ny in grids:
+            w = self.W.naca(alpha_deg, dtype=self.dtype, nx=nx, ny=ny)
+            lat = self.V.Lattice(self.V.config_of(w), device=self.device, stream=self.stream)
+            lat.set_body(self.V.body_of(w))
+            lats.append(lat)
+        batch = self.V.Batch(lats, stream=self.stream)
+        forms = batch.autotune(max(self.tune_trials, 1))
+        batch.close()
+        for (nx, ny), v, lat in zip(grids, forms, lats):
+            self.forms[(nx, ny)] = v
+            lat.close()
+        return dict(self.forms)
 
     def form(self, w) -> int:
         """The launch form for the workload's grid size: the tuner's choice on

@@ -97,3 +97,27 @@ def test_sedimentation_trajectory_is_a_settling_fall():
         assert np.all(np.abs(y[10:] - integral[10:]) <= 0.01 * np.abs(y[10:]))
         falls[est] = -y[-1]
     assert abs(falls["mem"] - falls["sim"]) <= 0.05 * falls["mem"]
+
+
+def test_naca2048_run_is_a_lifting_airfoil_in_a_low_mach_stream():
+    """The stored 4000-step run of the 2048 x 1024 airfoil at 20 degrees:
+    the sampled nodes are the seeded draw the file names; the stream stays at
+    low Mach number (|u| well below the lattice sound speed 1/sqrt(3), rho
+    within 5 % of 1); drag and lift are positive at a positive angle of
+    attack, lift above drag, in the mean over the second half of the run
+    (acoustic waves of the impulsive start still cross the lattice, and the
+    force of a single step can change sign); MEM and SIM, two estimates of
+    one force, agree within 5 % in that mean."""
+    d = load("naca2048_run.json")
+    n = len(d["nodes"])
+    idx = np.random.Generator(np.random.PCG64(d["seed"])).integers(0, 2048 * 1024, n)
+    assert np.array_equal(idx, np.array(d["nodes"]))
+    rho, ux, uy = (np.array(d[k]) for k in ("rho", "ux", "uy"))
+    assert np.abs(rho - 1).max() < 0.05 and np.hypot(ux, uy).max() < 0.2
+    mem, sim = np.array(d["mem"]), np.array(d["sim"])
+    assert len(mem) == len(sim) == d["steps"] // d["every"]
+    late = slice(len(mem) // 2, None)
+    fm, fs = mem[late, :2].mean(axis=0), sim[late, :2].mean(axis=0)
+    for f in (fm, fs):
+        assert f[0] > 0 and f[1] > f[0]
+    assert np.all(np.abs(fm - fs) <= 0.05 * np.abs(fs))

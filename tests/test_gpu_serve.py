@@ -61,15 +61,19 @@ ENVELOPES = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
                          "storage_envelopes.json")
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f16"])
+@pytest.mark.parametrize("dtype", ["f32", "f16", "f16sr"])
 def test_seeded_subset_matches_the_oracle(dtype):
     """The first eight requests of the seeded 256-request mix (their grids,
     768 x 384 .. 2048 x 1024, and angles), served together for 3000 steps
     each: every request's last window means of Cd and Cl (MEM and SIM) against
     the FP64 oracle's (tests/golden/serving_subset.json).  FP32 within the
-    1e-3 bar; FP16 offsets within three times the largest force error that
-    FP16 storage alone causes in the oracle (tests/golden/storage_envelopes.json,
-    free-stream offsets)."""
+    1e-3 bar; the 16-bit forms (FP16 rounded to nearest, and stochastically:
+    the form the serving benchmark serves) within three times the largest
+    force error that their storage rounding alone causes in the oracle
+    (tests/golden/storage_envelopes.json, free-stream offsets).  The worst
+    error is printed beside the 1e-3 target: a 1000-step window mean keeps
+    more of the stochastic rounding's noise than the 10,000-step means that
+    meet the target."""
     ref = json.load(open(SUBSET))
     reqs = [W.Request(r.rid, 0.0, r.alpha_deg, r.nx, r.ny)
             for r in W.serving_requests(256)[:len(ref["requests"])]]
@@ -80,15 +84,16 @@ def test_seeded_subset_matches_the_oracle(dtype):
         bar = 1e-3
     else:
         env = json.load(open(ENVELOPES))["cases"]
-        bar = 3 * max(max(env[f"{c}/free-stream/f16"]["force_mem"],
-                          env[f"{c}/free-stream/f16"]["force_sim"])
+        bar = 3 * max(max(env[f"{c}/free-stream/{dtype}"]["force_mem"],
+                          env[f"{c}/free-stream/{dtype}"]["force_sim"])
                       for c in ("naca0-512", "naca10-512"))
-    worst = 0.0
+    errs = []
     for g in ref["requests"]:
         r = got[g["rid"]]
         assert r.steps == ref["steps"] and not r.converged
         for k, v in (("cd_mem", r.cd), ("cl_mem", r.cl), ("cd_sim", r.cd_sim), ("cl_sim", r.cl_sim)):
-            err = abs(v - g[k]) / max(abs(g[k]), 1e-2)
-            worst = max(worst, err)
-            assert err <= bar, (dtype, g["rid"], k, v, g[k], err, bar)
-    print(dtype, "worst relative error of the served means", worst, "bar", bar)
+            errs.append((abs(v - g[k]) / max(abs(g[k]), 1e-2), g["rid"], k, v, g[k]))
+    worst = max(errs)
+    print(dtype, "worst relative error of the served means", worst, "bar", bar,
+          "coefficients above 1e-3:", sum(e[0] > 1e-3 for e in errs), "of", len(errs))
+    assert worst[0] <= bar, (dtype, worst, bar)
