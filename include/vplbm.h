@@ -379,7 +379,16 @@ vplbm_status vplbm_batch_step(vplbm_batch *batch, int32_t nsteps);
 
 /* vplbm_prepare for every lattice of the batch (the runs of a batch call are
  * at most 32 steps per lattice; each graph is uploaded on its lattice's chain
- * stream).  ESTATE when a lattice has no body placed. */
+ * stream).  It also builds a call of nsteps steps as one graph: every
+ * lattice's run of step graphs as a chain of child graphs, the chains side by
+ * side, for the lattices' current buffers and for the other ones (where they
+ * stand after an odd step count).  A later vplbm_batch_step of nsteps steps
+ * is then one graph launch on the batch's stream, as long as every lattice
+ * starts from a buffer it was built for and none of the step graphs was
+ * rebuilt since (vplbm_set_body, vplbm_load_state, a change of launch form);
+ * other calls take the per-lattice path, with the same results.  At most
+ * eight such graphs are kept per batch.  Synchronises.  ESTATE when a
+ * lattice has no body placed. */
 vplbm_status vplbm_batch_prepare(vplbm_batch *batch, int32_t nsteps);
 
 /* The bulk kernel's launch form per lattice of the batch, timed on the

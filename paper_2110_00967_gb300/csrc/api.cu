@@ -254,6 +254,7 @@ struct vplbm_ctx {
   uint64_t generation = 0;  // bumped whenever captured step graphs go stale
   // graphs[p][n]: n steps starting from buffer p, ending with finalized forces
   cudaGraphExec_t graphs[2][kGraphMax + 1] = {};
+  cudaGraph_t graph_defs[2][kGraphMax + 1] = {};  // their definitions (batch graphs clone them)
   bool graph_wanted[kGraphMax + 1] = {};  // lengths beyond the powers of two
   bool graphs_ready = false;
   cudaStream_t side = nullptr;      // the special kernel's stream
@@ -421,16 +422,27 @@ void drop_graphs(vplbm_ctx *c) {
         cudaGraphExecDestroy(g);
         g = nullptr;
       }
+  for (auto &row : c->graph_defs)
+    for (cudaGraph_t &g : row)
+      if (g) {
+        cudaGraphDestroy(g);
+        g = nullptr;
+      }
   c->graphs_ready = false;
+  ++c->generation;  // batch graphs made of these go stale
 }
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-// the longest captured graph that fits in `left` steps
-int graph_length(const vplbm_ctx *c, int left) {
+// the longest captured graph from buffer cur that fits in `left` steps
+int graph_length_from(const vplbm_ctx *c, int cur, int left) {
   for (int n = std::min(left, kGraphMax); n > 1; --n)
-    if (c->graphs[c->cur][n]) return n;
+    if (c->graphs[cur][n]) return n;
   return 1;
+}
+
+int graph_length(const vplbm_ctx *c, int left) {
+  return graph_length_from(c, c->cur, left);
 }
 
 // Captures the step graphs of every wanted length (the powers of two up to
@@ -475,7 +487,7 @@ vplbm_status ensure_graphs(vplbm_ctx *c, cudaStream_t s) {
         return cuda_fail(c, e2, "cudaStreamEndCapture");
       }
       e = cudaGraphInstantiate(&c->graphs[p][n], g, 0);
-      cudaGraphDestroy(g);
+      c->graph_defs[p][n] = g;
       if (e != cudaSuccess) {
         c->graphs[p][n] = nullptr;
         drop_graphs(c);
@@ -1366,8 +1378,20 @@ const char *vplbm_last_error(const vplbm_ctx *c) { return c ? c->err.c_str() : g
 // batches
 // ---------------------------------------------------------------------------
 
+// One launch for a whole call of n steps: every lattice's run of step graphs
+// (the graphs run_steps would launch) as a chain of child graphs, the chains
+// side by side in one graph.  Valid while each lattice starts from the buffer
+// and the step graphs it was built from.
+struct BatchGraph {
+  int n = 0;
+  std::vector<int> cur;
+  std::vector<uint64_t> gen;
+  cudaGraphExec_t exec = nullptr;
+};
+
 struct vplbm_batch {
   std::vector<vplbm_ctx *> ctxs;
+  std::vector<BatchGraph> graphs;   // for prepared step counts
   cudaStream_t stream = nullptr;
   std::vector<cudaEvent_t> ev_in;   // each lattice's stream -> the batch stream
   cudaEvent_t ev_out = nullptr;     // the batch stream -> each lattice's stream
@@ -1410,6 +1434,77 @@ cudaError_t batch_join(vplbm_batch *b, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_chain[q], 0);
   }
   return e;
+}
+
+// Every lattice replays step graphs (no per-step launches) from where it is.
+bool batch_graphable(const vplbm_batch *b) {
+  for (const vplbm_ctx *c : b->ctxs)
+    if (c->sim_every > 1 || c->pre || !c->graphs_ready) return false;
+  return true;
+}
+
+// The step graphs of a call of n steps of lattice c from buffer cur, in the
+// order vplbm_batch_step's rounds of at most kGraphMax steps launch them.
+template <typename F>
+void for_pieces(const vplbm_ctx *c, int cur, int n, F piece) {
+  for (int left = n; left > 0; left -= std::min(left, kGraphMax))
+    for (int r = std::min(left, kGraphMax); r > 0;) {
+      const int len = graph_length_from(c, cur, r);
+      piece(cur, len);
+      cur ^= len & 1;
+      r -= len;
+    }
+}
+
+const BatchGraph *find_batch_graph(const vplbm_batch *b, int n) {
+  for (const BatchGraph &bg : b->graphs) {
+    if (bg.n != n) continue;
+    bool ok = true;
+    for (size_t k = 0; k < b->ctxs.size() && ok; ++k)
+      ok = bg.cur[k] == b->ctxs[k]->cur && bg.gen[k] == b->ctxs[k]->generation;
+    if (ok) return &bg;
+  }
+  return nullptr;
+}
+
+constexpr size_t kBatchGraphsKept = 8;
+
+// Builds (and uploads on s) the batch graph of n steps from the buffers cur.
+vplbm_status build_batch_graph(vplbm_batch *b, int n, const std::vector<int> &cur, cudaStream_t s) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  for (size_t k = 0; k < b->ctxs.size() && e == cudaSuccess; ++k) {
+    const vplbm_ctx *c = b->ctxs[k];
+    cudaGraphNode_t prev = nullptr;
+    for_pieces(c, cur[k], n, [&](int p, int len) {
+      if (e != cudaSuccess) return;
+      if (!c->graph_defs[p][len]) {
+        e = cudaErrorInvalidValue;
+        return;
+      }
+      cudaGraphNode_t node = nullptr;
+      e = cudaGraphAddChildGraphNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0,
+                                     c->graph_defs[p][len]);
+      prev = node;
+    });
+  }
+  BatchGraph bg;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&bg.exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e == cudaSuccess) e = cudaGraphUpload(bg.exec, s);
+  if (e != cudaSuccess) {
+    if (bg.exec) cudaGraphExecDestroy(bg.exec);
+    return batch_cuda(e, "building a batch graph");
+  }
+  bg.n = n;
+  bg.cur = cur;
+  for (const vplbm_ctx *c : b->ctxs) bg.gen.push_back(c->generation);
+  if (b->graphs.size() >= kBatchGraphsKept) {
+    cudaGraphExecDestroy(b->graphs.front().exec);
+    b->graphs.erase(b->graphs.begin());
+  }
+  b->graphs.push_back(std::move(bg));
+  return VPLBM_OK;
 }
 
 }  // namespace
@@ -1521,6 +1616,26 @@ vplbm_status vplbm_batch_prepare(vplbm_batch *b, int32_t nsteps) {
   for (cudaStream_t st : b->chain)
     if (const cudaError_t e = cudaStreamSynchronize(st); e != cudaSuccess)
       return batch_cuda(e, "vplbm_batch_prepare: cudaStreamSynchronize");
+  // a call of nsteps steps as one graph launch, from the current buffers and
+  // from the other ones (where the lattices stand after an odd step count)
+  if (nsteps > 0 && batch_graphable(b)) {
+    std::vector<int> cur;
+    for (const vplbm_ctx *c : b->ctxs) cur.push_back(c->cur);
+    for (int flip = 0; flip < 2; ++flip) {
+      std::vector<int> from(cur);
+      for (int &p : from) p ^= flip;
+      bool have = false;
+      for (const BatchGraph &bg : b->graphs)
+        if (bg.n == nsteps && bg.cur == from) {
+          have = true;
+          for (size_t k = 0; k < b->ctxs.size() && have; ++k) have = bg.gen[k] == b->ctxs[k]->generation;
+        }
+      if (!have)
+        if (vplbm_status st = build_batch_graph(b, nsteps, from, b->stream)) return st;
+    }
+    if (const cudaError_t e = cudaStreamSynchronize(b->stream); e != cudaSuccess)
+      return batch_cuda(e, "vplbm_batch_prepare: cudaStreamSynchronize");
+  }
   return VPLBM_OK;
 }
 
@@ -1542,6 +1657,30 @@ vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_in[k], 0);
     if (e != cudaSuccess) return batch_cuda(e, "vplbm_batch_step: ordering after a lattice stream");
   }
+  // a prepared step count: the whole call is one launch of the batch graph
+  if (batch_graphable(b))
+    if (const BatchGraph *bg = find_batch_graph(b, nsteps)) {
+      for (int k = 0; k < n; ++k)  // a graph starts with nothing pending
+        if (const cudaError_t e = flush_forces(b->ctxs[k], s); e != cudaSuccess)
+          return batch_cuda(e, "vplbm_batch_step: finalizing pending forces");
+      if (const cudaError_t e = cudaGraphLaunch(bg->exec, s); e != cudaSuccess)
+        return batch_cuda(e, "vplbm_batch_step: cudaGraphLaunch");
+      for (int k = 0; k < n; ++k) {
+        vplbm_ctx *c = b->ctxs[k];
+        for_pieces(c, c->cur, nsteps, [&](int, int len) {
+          c->launches += 2 * len + 1 + (c->body_host.moving ? 1 : 0);
+        });
+        c->steps += nsteps;
+        c->cur ^= nsteps & 1;
+        c->pending = false;
+        c->mask_stale = false;
+      }
+      cudaError_t e = cudaEventRecord(b->ev_out, s);
+      for (int k = 0; k < n && e == cudaSuccess; ++k)
+        if (b->ctxs[k]->stream != s) e = cudaStreamWaitEvent(b->ctxs[k]->stream, b->ev_out, 0);
+      if (e != cudaSuccess) return batch_cuda(e, "vplbm_batch_step: ordering of the lattice streams");
+      return VPLBM_OK;
+    }
   // each lattice runs its own steps (its step graphs where they apply) on its
   // chain, forked from s and joined back; the chains meet only at the end of
   // the call, so no lattice waits for another between runs of steps.  The
@@ -1566,6 +1705,8 @@ vplbm_status vplbm_batch_step(vplbm_batch *b, int32_t nsteps) {
 
 void vplbm_batch_destroy(vplbm_batch *b) {
   if (!b) return;
+  for (BatchGraph &bg : b->graphs)
+    if (bg.exec) cudaGraphExecDestroy(bg.exec);
   for (cudaEvent_t ev : b->ev_in)
     if (ev) cudaEventDestroy(ev);
   if (b->ev_out) cudaEventDestroy(b->ev_out);

@@ -193,3 +193,40 @@ def test_prepared_lengths_replay_one_graph_and_change_nothing():
     for a, m in zip(alone, members):
         same_state(a, m, 53)
     batch.close()
+
+
+def test_prepared_batch_call_is_one_graph_launch_and_changes_nothing():
+    """After vplbm_batch_prepare(20) a batch call of 20 steps replays one
+    graph holding every lattice's steps (from the current buffers, or from the
+    other ones after an odd count); calls of other lengths, and calls after a
+    member's launch form changed, take the per-lattice path.  Every lattice
+    (FP32 and FP16-stochastic airfoils, a falling disk) ends bit-identical,
+    forces, sums and body included, to the same lattice stepped alone."""
+    works = [W.naca(7.0, dtype="f32", nx=256, ny=128), W.naca(3.0, dtype="f16sr", nx=384, ny=192),
+             W.sedimentation("sim", steps=100)]
+    members = [lattice(w) for w in works]
+    alone = [lattice(w) for w in works]
+    batch = V.Batch(members)
+    batch.step(1)
+    batch.prepare(20)
+    counts = []
+    for n in (20, 20, 5, 20, 3, 20):
+        l0 = batch.launches
+        batch.step(n)
+        counts.append(batch.launches - l0)
+    members[0].bulk_variant = 2  # the batch graph goes stale: per-lattice path
+    batch.step(20)
+    batch.close()
+    total = 1 + 20 + 20 + 5 + 20 + 3 + 20 + 20
+    for w, a in zip(works, alone):
+        a.step(1 + 20 + 20 + 5 + 20 + 3 + 20)
+    alone[0].bulk_variant = 2
+    for a in alone:
+        a.step(20)
+    for a, m in zip(alone, members):
+        same_state(a, m, total)
+        np.testing.assert_array_equal(a.get_body(), m.get_body())
+        np.testing.assert_array_equal(a.get_mask(), m.get_mask())
+    # fixed bodies: 2 launches per step + 1 finalize; the falling disk adds
+    # one mask launch per graph
+    assert counts[0] == 2 * 20 * 3 + 3 + 1
