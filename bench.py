@@ -514,6 +514,7 @@ def run_serving(args, rank, world, local_rank):
         "p50_all_s": round(summ["p50_all_s"], 4), "p99_all_s": round(summ["p99_all_s"], 4),
         "converged": summ["converged"], "capped": summ["capped"],
         "rejected": summ["rejected"], "aggregate_mlups": round(world * summ["mlups"], 1),
+        "aggregate_gbs": round(world * summ["mlups"] * BYTES_PER_LUP[args.dtype] / 1e3, 1),
         "elapsed_s": round(elapsed, 3),
     }
 

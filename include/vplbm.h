@@ -356,7 +356,8 @@ vplbm_status vplbm_bulk_variant(vplbm_ctx *ctx, int32_t *variant);
  * lattice's steps are replayed from its own step graphs (runs of 1, 2, 4, ...,
  * 32 steps, as vplbm_step replays them) where they apply, and the lattices
  * meet only at the end of the call, so that none waits for another between
- * runs.  The parameter studies of Sec. 4 (one lattice per angle of attack, per
+ * runs; a step count prepared with vplbm_batch_prepare is one graph launch
+ * holding every lattice's runs side by side.  The parameter studies of Sec. 4 (one lattice per angle of attack, per
  * estimator, per resolution) are such batches; the paper itself steps one
  * lattice at a time. */
 typedef struct vplbm_batch vplbm_batch;
