@@ -3,7 +3,7 @@
 Requests (an angle of attack and a grid, arriving over time) are admitted
 while their workspaces fit in a device-memory budget, stepped together as one
 batch of lattices (`vplbm_batch_*`: each lattice on a stream of its own,
-32-step CUDA graphs), and retired when converged; the batch is re-formed
+replaying its own step graphs), and retired when converged; the batch is re-formed
 whenever its membership changes (continuous batching).  Convergence follows
 the time-averaging of Sec. 3.1: the means of Cd = 2F_x/(rho0 U0^2 C) and
 Cl = 2F_y/(rho0 U0^2 C) over consecutive windows of `window` steps (from the
