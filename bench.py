@@ -251,18 +251,20 @@ def run_ours(args, rank, world, local_rank):
     # the step graphs of a run of args.steps steps, captured before the timed
     # region (one graph per lattice for up to 32 steps)
     batch.prepare(args.steps)
+    # the clock sampler starts before the warm-up, so that the warm-up steps,
+    # not an idle wait, lead into the timed region
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
     batch.step(args.warmup)
     torch.cuda.synchronize()
 
     # device-timed region: every lattice advances args.steps steps
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = batch.launches
-    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     barrier(world)
     torch.cuda.synchronize()
-    if clocks:
-        clocks.start()
-        time.sleep(0.3)
     if args.profile_range:
         torch.cuda.profiler.start()
     start.record(stream)

@@ -97,3 +97,20 @@ def test_seeded_subset_matches_the_oracle(dtype):
     print(dtype, "worst relative error of the served means", worst, "bar", bar,
           "coefficients above 1e-3:", sum(e[0] > 1e-3 for e in errs), "of", len(errs))
     assert worst[0] <= bar, (dtype, worst, bar)
+
+
+def test_mix_tuning_records_a_form_per_grid_and_changes_no_result():
+    """The serving backend's tuner (the mix's grid sizes stepped together on
+    scratch lattices) records one launch form per size, and a request served
+    with the tuned forms gets the same bits as with the default forms."""
+    tuned = S.GpuBackend("f16sr", tune_trials=2)
+    forms = tuned.tune_mix([(256, 128), (384, 192)])
+    assert set(forms) == {(256, 128), (384, 192)} and all(0 <= v < 3 for v in forms.values())
+    req = W.Request(0, 0.0, 6.0, 384, 192)
+    lat = tuned.make(req)
+    assert lat.bulk_variant == forms[(384, 192)]
+    lat.close()
+    a = S.Server(tuned, memory_bytes=8 << 30, window=500, tol=0.0, cap=1000).run([req])[0]
+    b = S.Server(S.GpuBackend("f16sr"), memory_bytes=8 << 30, window=500, tol=0.0,
+                 cap=1000).run([req])[0]
+    assert (a.cd, a.cl, a.cd_sim, a.cl_sim) == (b.cd, b.cl, b.cd_sim, b.cl_sim)
