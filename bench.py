@@ -57,6 +57,7 @@ KERNEL_SOURCES = ("paper_2110_00967_gb300/csrc/step.cu",
                   "paper_2110_00967_gb300/csrc/api.cu")
 METRIC = "VP-LBM MLUPS"
 CHUNK = 32  # the longest step graph of a lattice
+E2E_RUNS = 3  # end-to-end solves timed; the median is reported
 HISTORY = 64  # force-history ring of each lattice
 def workload_name(dtype: str) -> str:
     return f"naca0012-re1000-2048x1024-{dtype}-alpha0,5,10,15,20"
@@ -291,18 +292,23 @@ def run_ours(args, rank, world, local_rank):
     n_chunks = e2e_steps // CHUNK
     pinned = torch.empty((len(lats), n_chunks, CHUNK, 9), dtype=torch.float64, pin_memory=True)
     rows = pinned.numpy()
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for w, lat in zip(works, lats):
-        lat.set_body(V.body_of(w))
-    for c in range(n_chunks):
-        batch.step(CHUNK)
-        for i, lat in enumerate(lats):
-            V.vplbm_force_history_async(lat.ctx, CHUNK, rows[i, c].ctypes.data)
-    torch.cuda.synchronize()
-    e2e_dt = reduce_max(time.perf_counter() - t0, world, dev)
-    assert np.isfinite(rows[:, :, :, :3]).all() and np.isfinite(rows[:, :, :, 3:6]).all()
+    # the median of E2E_RUNS such solves (wall-clock time is exposed to the
+    # host's own jitter, which one short run can catch)
+    e2e_runs = []
+    for _ in range(E2E_RUNS):
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for w, lat in zip(works, lats):
+            lat.set_body(V.body_of(w))
+        for c in range(n_chunks):
+            batch.step(CHUNK)
+            for i, lat in enumerate(lats):
+                V.vplbm_force_history_async(lat.ctx, CHUNK, rows[i, c].ctypes.data)
+        torch.cuda.synchronize()
+        e2e_runs.append(reduce_max(time.perf_counter() - t0, world, dev))
+        assert np.isfinite(rows[:, :, :, :3]).all() and np.isfinite(rows[:, :, :, 3:6]).all()
+    e2e_dt = sorted(e2e_runs)[len(e2e_runs) // 2]
     # host -> device per lattice and set_body: the body state and the force region (two
     # buffers each, 152 and 24 bytes) and the 849 SIM points (72 bytes each)
     h2d = len(lats) * (2 * 152 + 2 * 24 + 849 * 72) / e2e_steps
@@ -336,7 +342,8 @@ def run_ours(args, rank, world, local_rank):
                      "bytes_per_lup": bpl, "peak_kind": peak_kind},
         "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps},
+                "steps": e2e_steps, "runs": E2E_RUNS, "statistic": "median",
+                "all_mlups": [round(world * nodes * e2e_steps / t / 1e6, 1) for t in e2e_runs]},
         "gpu_launches": launches,
         "clocks": clk,
     }

@@ -165,7 +165,11 @@ vplbm_status vplbm_set_stream(vplbm_ctx *ctx, void *cuda_stream);
  * force histories and averages, and sets the initial state f = feq(1, u0)
  * with u0 = u_in on fluid nodes and the rigid velocity on solid nodes.
  * kind NONE gives an empty lattice.  EINVAL when the body does not fit in
- * the lattice, n_sim_points exceeds the capacity, or a NACA body is moving. */
+ * the lattice, n_sim_points exceeds the capacity, or a NACA body is moving.
+ * The step graphs (vplbm_step) are kept when the new body has the same SIM
+ * point count and constant part, force-region block count, motion and SIM
+ * cadence as the old one (the same body placed again); otherwise they are
+ * dropped and captured again at the next run.  Synchronises the stream. */
 vplbm_status vplbm_set_body(vplbm_ctx *ctx, const vplbm_body *body);
 
 /* Queues nsteps time steps (nsteps >= 0).  One step, for every node:

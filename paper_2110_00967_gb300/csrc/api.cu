@@ -455,6 +455,7 @@ int graph_length(const vplbm_ctx *c, int left) {
 // stream s that will launch it.
 vplbm_status ensure_graphs(vplbm_ctx *c, cudaStream_t s) {
   if (c->graphs_ready) return VPLBM_OK;
+  VPLBM_CUDA(c, flush_forces(c, s));  // the graphs start with nothing pending
   if (!c->capture_stream)
     VPLBM_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
   const int64_t launches = c->launches;
@@ -795,16 +796,26 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
     cfy += ty;
     ctq += p.dx * ty - p.dy * tx;
   }
+  // The step graphs carry, by value, what a body sets beyond its device data:
+  // the SIM point count and constant part, the region's block count, whether
+  // it moves, the SIM cadence.  A body with the same ones (the same body placed
+  // again, as a restarted solve does) keeps them: its geometry and state are
+  // read from device memory at every step.
+  const int new_slots = std::max(1, slots);
+  const int new_every = (b->moving && b->estimator == VPLBM_SIM) ? 1 : c->cfg.sim_every;
+  const double new_const[3] = {cfx, cfy, ctq};
+  const bool keep_graphs = c->has_body && c->n_sim == n_sim && c->region_slots == new_slots &&
+                           c->body_host.moving == bs.moving && c->sim_every == new_every &&
+                           std::memcmp(c->sim_const, new_const, sizeof(new_const)) == 0;
   c->sim_const[0] = cfx;
   c->sim_const[1] = cfy;
   c->sim_const[2] = ctq;
   c->body_cfg = *b;
   c->body_host = bs;
-  c->region_slots = std::max(1, slots);
+  c->region_slots = new_slots;
   c->n_sim = n_sim;
-  c->sim_every = (b->moving && b->estimator == VPLBM_SIM) ? 1 : c->cfg.sim_every;
-  drop_graphs(c);
-  ++c->generation;
+  c->sim_every = new_every;
+  if (!keep_graphs) drop_graphs(c);
   cudaStream_t s = c->stream;
   c->region_host = reg;
   for (int k = 0; k < 2; ++k) {

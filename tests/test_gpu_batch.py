@@ -230,3 +230,20 @@ def test_prepared_batch_call_is_one_graph_launch_and_changes_nothing():
     # fixed bodies: 2 launches per step + 1 finalize; the falling disk adds
     # one mask launch per graph
     assert counts[0] == 2 * 20 * 3 + 3 + 1
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16sr"])
+def test_placing_the_body_again_restarts_the_solve_exactly(dtype):
+    """vplbm_set_body on a lattice that has stepped: with the same body (its
+    step graphs kept) and with another angle (graphs captured again), the
+    lattice then steps exactly as a fresh lattice with that body does."""
+    w5, w7 = (W.naca(a, dtype=dtype, nx=256, ny=128) for a in (5.0, 7.0))
+    again, other, fresh5, fresh7 = lattice(w5), lattice(w5), lattice(w5), lattice(w7)
+    for lat in (again, other):
+        lat.step(37)
+    again.set_body(V.body_of(w5))
+    other.set_body(V.body_of(w7))
+    for lat in (again, other, fresh5, fresh7):
+        lat.step(45)
+    same_state(again, fresh5, 45)
+    same_state(other, fresh7, 45)
