@@ -247,3 +247,35 @@ def test_placing_the_body_again_restarts_the_solve_exactly(dtype):
         lat.step(45)
     same_state(again, fresh5, 45)
     same_state(other, fresh7, 45)
+
+
+def test_batch_on_its_own_stream_orders_the_lattices_streams():
+    """Lattices created on streams of their own, batched on a third stream:
+    work queued on a lattice's stream before a batch call runs before it,
+    and work queued there after the call runs after it (the batch call is a
+    prepared one-graph launch and an unprepared one), so that the states and
+    the host read-backs match lattices stepped alone."""
+    import torch
+    w = W.naca(9.0, dtype="f32", nx=256, ny=128)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    members = []
+    for st in streams:
+        lat = V.Lattice(V.config_of(w), stream=st)
+        lat.set_body(V.body_of(w))
+        members.append(lat)
+    alone = lattice(w)
+    batch_stream = torch.cuda.Stream()
+    batch = V.Batch(members, stream=batch_stream)
+    members[0].step(3)  # on its own stream, before the batch's calls
+    batch.step(1)
+    batch.prepare(16)
+    batch.step(16)
+    batch.step(7)
+    for lat in members:
+        lat.step(2)  # on its own stream, after the batch's calls
+    batch.close()
+    alone.step(3 + 1 + 16 + 7 + 2)
+    same_state(alone, members[0], 29)
+    other = lattice(w)
+    other.step(1 + 16 + 7 + 2)
+    same_state(other, members[1], 26)
