@@ -203,6 +203,8 @@ bool build_polygon(const vplbm_body &b, int n, std::vector<SimPoint> &pts) {
     p.f_nx = (float)p.nx;
     p.f_ny = (float)p.ny;
     p.f_s = (float)p.s;
+    p.n_cand = -1;  // walked every step, unless a fixed body's walk is cached
+    for (uint32_t &q : p.cand) q = 0u;
   }
   return true;
 }
@@ -841,6 +843,11 @@ vplbm_status vplbm_set_body(vplbm_ctx *c, const vplbm_body *b) {
   }
   VPLBM_CUDA(c, launch_init(storage_dtype(c->cfg.dtype), L, c->body[0], c->chi, c->buf[0], c->cfg.u_in[0], c->cfg.u_in[1], s));
   ++c->launches;
+  // a fixed body's SIM points sample the same nodes at every step: walk once
+  if (n_sim > 0 && !b->moving && L.nx <= 0xffff && L.ny <= 0xffff) {
+    VPLBM_CUDA(c, launch_sim_cache(step_args(c, 0, true), s));
+    ++c->launches;
+  }
   // histories, sums, counters, status
   VPLBM_CUDA(c, cudaMemsetAsync(c->ws + c->lay.hist, 0, c->lay.body[0] - c->lay.hist, s));
   VPLBM_CUDA(c, cudaMemsetAsync(c->ws + c->lay.sums, 0, c->lay.total - c->lay.sums, s));
@@ -1191,7 +1198,7 @@ struct SnapHeader {
   uint64_t tail_bytes, pop_bytes;
 };
 constexpr char kSnapMagic[8] = {'V', 'P', 'L', 'B', 'M', 'S', 'N', 'P'};
-constexpr int32_t kSnapVersion = 2;
+constexpr int32_t kSnapVersion = 3;  // 3: SIM points carry their cached walk
 
 size_t snap_header_bytes() { return align_up(sizeof(SnapHeader), 64); }
 size_t snap_tail_bytes(const vplbm_ctx *c) { return c->lay.total - c->lay.prev[0]; }

@@ -170,57 +170,85 @@ __device__ __forceinline__ void sim_geom<float>(const SimPoint &sp, float &dx, f
   dx = sp.f_dx; dy = sp.f_dy; nx = sp.f_nx; ny = sp.f_ny; s = sp.f_s;
 }
 
-// One SIM integration point: the nearest node (both nodes when the point lies
-// exactly half-way: the coordinates are compared in FP64), the walk along the
-// direction closest to the normal to the first fluid node, the stress
-// averaged over the candidates, then S (sigma + I/3) n and its moment; the
-// -(1/3) S n part sums to a constant of the polygon added in the tail.
+// The sampled nodes of SIM point sp for the reference point (bxg, byg): the
+// nearest node (both nodes when the point lies exactly half-way: the
+// coordinates are compared in FP64), each walked along the direction closest
+// to the normal to the first fluid node.  Returns their count (1, 2 or 4; 0
+// when a walk finds no fluid node), the nodes packed i | j << 16 in the order
+// the stress sum takes them.
+__device__ __forceinline__ int sim_candidates(const StepArgs &p, const SimPoint &sp, double bxg,
+                                              double byg, uint32_t (&cand)[4]) {
+  const double x = bxg + sp.dx, y = byg + sp.dy;
+  const double rx = floor(x + 0.5), ry = floor(y + 0.5);
+  const int ncx = (rx == x + 0.5) ? 2 : 1, ncy = (ry == y + 0.5) ? 2 : 1;
+  int n = 0;
+  for (int u = 0; u < ncy; ++u)
+    for (int v = 0; v < ncx; ++v) {
+      int qi, qj;
+      if (!sim_walk(p, sp.dir, (int)rx - v, (int)ry - u, qi, qj)) return 0;
+      cand[n++] = (uint32_t)qi | ((uint32_t)qj << 16);
+    }
+  return n;
+}
+
+// The walks of a fixed body's SIM points, once when the body is placed (the
+// mask never changes afterwards): one thread per point.
+__global__ void sim_cache_kernel(const StepArgs p) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= p.n_sim) return;
+  SimPoint *sp = const_cast<SimPoint *>(p.sim_pts) + q;
+  uint32_t cand[4] = {0u, 0u, 0u, 0u};
+  const int n = sim_candidates(p, *sp, p.body_src->xg, p.body_src->yg, cand);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sp->cand[k] = cand[k];
+  sp->n_cand = n;
+}
+
+// One SIM integration point: its sampled nodes (walked now, or for a fixed
+// body found when it was placed), the stress averaged over them, then
+// S (sigma + I/3) n and its moment; the -(1/3) S n part sums to a constant of
+// the polygon added in the tail.
 template <typename S, bool kGather>
 __device__ __noinline__ FixAcc<typename Store<S>::T> sim_point(const StepArgs &p, const S *buf, double bxg, double byg,
                                          int q, bool &missing) {
   using T = typename Store<S>::T;
   const SimPoint sp = p.sim_pts[q];
-  const double x = bxg + sp.dx, y = byg + sp.dy;
-  const double rx = floor(x + 0.5), ry = floor(y + 0.5);
-  const int ncx = (rx == x + 0.5) ? 2 : 1, ncy = (ry == y + 0.5) ? 2 : 1;
+  uint32_t cand[4] = {sp.cand[0], sp.cand[1], sp.cand[2], sp.cand[3]};
+  const int n = sp.n_cand >= 0 ? sp.n_cand : sim_candidates(p, sp, bxg, byg, cand);
   const T *prev = static_cast<const T *>(p.prev_src);
   T sig[3] = {0, 0, 0};
   int first = -1;
-  bool ok = true;
-  for (int u = 0; u < ncy && ok; ++u)
-    for (int v = 0; v < ncx && ok; ++v) {
-      int qi, qj;
-      if (!sim_walk(p, sp.dir, (int)rx - v, (int)ry - u, qi, qj)) {
-        ok = false;
-        break;
+  const bool ok = n > 0;
+  for (int k = 0; k < n; ++k) {
+    const int qi = (int)(cand[k] & 0xffffu), qj = (int)(cand[k] >> 16);
+    if (first < 0) first = qj * p.L.nx + qi;
+    T s3[3];
+    node_stress<S, kGather>(buf, prev, p.L, Consts<T>(p), qi, qj, s3);
+    if (p.sim_order == 1) {
+      // first order: extrapolated to the point along the direction from
+      // the next node, where that node is fluid and inside the lattice
+      const int ni = qi + cx_of(sp.dir), nj = qj + cy_of(sp.dir);
+      if (ni >= 0 && ni < p.L.nx && nj >= 0 && nj < p.L.ny && !(solid_at(p, ni, nj) & kSolid)) {
+        T s3n[3];
+        node_stress<S, kGather>(buf, prev, p.L, Consts<T>(p), ni, nj, s3n);
+        const double x = bxg + sp.dx, y = byg + sp.dy;
+        const int c2 = cx_of(sp.dir) * cx_of(sp.dir) + cy_of(sp.dir) * cy_of(sp.dir);
+        const T t = (T)(((x - qi) * cx_of(sp.dir) + (y - qj) * cy_of(sp.dir)) / (double)c2);
+        s3[0] += t * (s3n[0] - s3[0]);
+        s3[1] += t * (s3n[1] - s3[1]);
+        s3[2] += t * (s3n[2] - s3[2]);
       }
-      if (first < 0) first = qj * p.L.nx + qi;
-      T s3[3];
-      node_stress<S, kGather>(buf, prev, p.L, Consts<T>(p), qi, qj, s3);
-      if (p.sim_order == 1) {
-        // first order: extrapolated to the point along the direction from
-        // the next node, where that node is fluid and inside the lattice
-        const int ni = qi + cx_of(sp.dir), nj = qj + cy_of(sp.dir);
-        if (ni >= 0 && ni < p.L.nx && nj >= 0 && nj < p.L.ny && !(solid_at(p, ni, nj) & kSolid)) {
-          T s3n[3];
-          node_stress<S, kGather>(buf, prev, p.L, Consts<T>(p), ni, nj, s3n);
-          const int c2 = cx_of(sp.dir) * cx_of(sp.dir) + cy_of(sp.dir) * cy_of(sp.dir);
-          const T t = (T)(((x - qi) * cx_of(sp.dir) + (y - qj) * cy_of(sp.dir)) / (double)c2);
-          s3[0] += t * (s3n[0] - s3[0]);
-          s3[1] += t * (s3n[1] - s3[1]);
-          s3[2] += t * (s3n[2] - s3[2]);
-        }
-      }
-      sig[0] += s3[0];
-      sig[1] += s3[1];
-      sig[2] += s3[2];
     }
+    sig[0] += s3[0];
+    sig[1] += s3[1];
+    sig[2] += s3[2];
+  }
   p.sim_nodes[q] = ok ? first : -1;
   missing = !ok;
   FixAcc<T> r;
   if (!ok) return r;
   // mean over 1, 2 or 4 candidates: an exact power-of-two scaling
-  const T inv = (ncx * ncy == 1) ? (T)1 : ((ncx * ncy == 2) ? (T)0.5 : (T)0.25);
+  const T inv = (n == 1) ? (T)1 : ((n == 2) ? (T)0.5 : (T)0.25);
   T dx, dy, nx, ny, sl;
   sim_geom<T>(sp, dx, dy, nx, ny, sl);
   const T sxx = sig[0] * inv, sxy = sig[1] * inv, syy = sig[2] * inv;
@@ -1413,6 +1441,12 @@ cudaError_t launch_finalize(int dtype, const StepArgs &a, cudaStream_t s) {
 
 cudaError_t launch_mask(const StepArgs &a, cudaStream_t s) {
   mask_kernel<<<a.region_slots, dim3(kTileX, kTileY), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sim_cache(const StepArgs &a, cudaStream_t s) {
+  if (a.n_sim <= 0) return cudaSuccess;
+  sim_cache_kernel<<<(a.n_sim + 127) / 128, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

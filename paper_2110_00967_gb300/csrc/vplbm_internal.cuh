@@ -150,6 +150,13 @@ struct SimPoint {
   double s;       // edge length S_i
   int32_t dir;    // lattice direction closest to the normal
   float f_dx, f_dy, f_nx, f_ny, f_s;  // FP32 copies for FP32 paths
+  // For a fixed body, the walk's result, found once when the body is placed:
+  // the sampled fluid nodes (i in the low 16 bits, j in the high 16), in the
+  // order the walk takes them (one, or two or four for a point half-way
+  // between nodes).  n_cand: their count; 0 when no fluid node was found;
+  // -1 when not cached (a moving body, whose nodes are walked every step).
+  int32_t n_cand;
+  uint32_t cand[4];
 };
 
 // body reference point and rigid velocity in the compute type
@@ -595,6 +602,9 @@ cudaError_t launch_finalize(int dtype, const StepArgs &a, cudaStream_t s);
 // chi of a moving body at the current time level on the force-region tiles
 // (reg_src, body_src): the mask the read-backs see after a call
 cudaError_t launch_mask(const StepArgs &a, cudaStream_t s);
+// the walks of a fixed body's SIM points, stored in the points (sim_pts,
+// n_sim, chi, body_src of a)
+cudaError_t launch_sim_cache(const StepArgs &a, cudaStream_t s);
 // the bulk kernel: the nodes off the edges, outside the force-region tiles
 // the bulk kernel in one of kBulkVariants launch forms (same results, bit
 // for bit): FP32 and FP64 blocks of 1, 2 or 4 tiles; 16-bit storage with
