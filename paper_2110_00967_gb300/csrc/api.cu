@@ -313,7 +313,8 @@ StepArgs step_args(vplbm_ctx *c, int src, bool do_sim) {
   a.sim_nodes = c->sim_nodes;
   a.n_sim = c->n_sim;
   a.sim_order = c->cfg.sim_order;
-  a.sim_blocks = do_sim ? (c->n_sim + kThreads - 1) / kThreads : 0;
+  a.sim_per_block = c->body_host.moving ? kSimPointsMoving : kSimPointsFixed;
+  a.sim_blocks = do_sim ? (c->n_sim + a.sim_per_block - 1) / a.sim_per_block : 0;
   a.hist = c->hist;
   a.hist_len = effective_hist(c->cfg);
   a.sums = c->sums;

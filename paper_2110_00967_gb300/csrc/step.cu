@@ -933,10 +933,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) special_kernel(const Ste
 
   if (b < p.sim_blocks) {
     // ---- SIM points of this level ----
-    const int q = b * kThreads + tid;
+    const int q = b * p.sim_per_block + tid;
     FixAcc<T> acc;
     bool missing = false;
-    if (q < p.n_sim) {
+    if (tid < p.sim_per_block && q < p.n_sim) {
       const BodyState *body = p.body_src;
       acc = sim_point<S, kGather>(p, static_cast<const S *>(p.src), body->xg, body->yg, q,
                                   missing);

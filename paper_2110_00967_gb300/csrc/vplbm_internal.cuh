@@ -44,7 +44,12 @@ constexpr int kTileX = 128;
 constexpr int kTileY = 2;
 constexpr int kThreads = kTileX * kTileY;
 constexpr int kRegionCapacity = 16384;  // force-region tiles
-constexpr int kSimThreads = 128;        // threads per SIM block
+// SIM points per block of the special kernel: a fixed body's points read
+// their cached nodes (memory latency only); a moving body's walk evaluates the
+// body's FP64 predicate, and GB300's FP64 rate per SM is low, so its points
+// are spread over more blocks (more SMs)
+constexpr int kSimPointsFixed = kThreads;
+constexpr int kSimPointsMoving = 32;
 
 // mask byte bits
 constexpr uint8_t kSolid = 1;      // chi = 1
@@ -430,6 +435,7 @@ struct StepArgs {
   int32_t n_sim;
   int32_t sim_order;     // 0: stress copied from the sampled node; 1: extrapolated linearly
   int32_t sim_blocks;    // leading blocks that evaluate SIM (0: SIM not due)
+  int32_t sim_per_block; // SIM points per block (a multiple of 32)
   double *hist;          // [hist_len][6]
   int32_t hist_len;
   int32_t pad0;
