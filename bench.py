@@ -70,7 +70,7 @@ def config_block(dtype: str = "f32", extra=None):
          "storage": "f32" if dtype == "f32" else f"{dtype} offsets from feq(1, u_in)",
          "forces_per_step": ["mem", "sim-849"],
          "l2": f"inputs larger than L2: 5 lattices x {mb} MB ping-pong, stepped side by side"
-               + (" (ncu range replay: DRAM traffic 152.7 MB per lattice step, 151.0 algorithmic)"
+               + (" (ncu range replay: DRAM traffic 151.9 MB per lattice step, 151.0 algorithmic)"
                   if dtype == "f32" else "")}
     if extra:
         c.update(extra)
