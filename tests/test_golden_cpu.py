@@ -121,3 +121,33 @@ def test_naca2048_run_is_a_lifting_airfoil_in_a_low_mach_stream():
     for f in (fm, fs):
         assert f[0] > 0 and f[1] > f[0]
     assert np.all(np.abs(fm - fs) <= 0.05 * np.abs(fs))
+
+
+def test_stochastic_rounding_emulation_is_unbiased_and_picks_neighbours():
+    """The oracle-side emulation of stochastic rounding that the storage
+    envelopes use: each rounded value is one of the two 16-bit neighbours of
+    the FP64 value (equal to it when representable), and the mean of many
+    roundings of one value is the value (unbiased), for FP16 (normal and
+    subnormal) and BF16, both signs."""
+    import importlib.util
+    path = os.path.join(GOLDEN, "make_storage_envelopes.py")
+    spec = importlib.util.spec_from_file_location("make_storage_envelopes", path)
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    m.RNG = np.random.Generator(np.random.PCG64(7))
+    n = 200_000
+    for fmt, vals in (("f16sr", (1.0 + 0.3 * 2 ** -10, -0.75 - 0.71 * 2 ** -11, 0.4 * 2 ** -24,
+                                 3.0e-6, 0.25)),
+                      ("bf16sr", (1.0 + 0.3 * 2 ** -7, -0.011 - 0.6 * 2 ** -14, 0.5))):
+        for v in vals:
+            h = np.full(n, v)
+            lo, hi = m.neighbours(h[:1], fmt[:-2])
+            r = m.round_to(h, fmt)
+            assert np.all((r == lo[0]) | (r == hi[0])), (fmt, v)
+            gap = hi[0] - lo[0]
+            if gap == 0:
+                assert np.all(r == v)
+                continue
+            p = (v - lo[0]) / gap
+            # the mean's error within five standard errors of a Bernoulli draw
+            assert abs(r.mean() - v) <= 5 * gap * np.sqrt(p * (1 - p) / n) + 1e-300, (fmt, v)
